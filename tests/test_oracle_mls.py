@@ -1,0 +1,320 @@
+"""Pins for the oracle's step 2 (support radius, local regularised MLS).
+
+The checks come from what the paper fixes: reproduction of Pi_K^tan at the
+centre when tau = 0 and of constants for every tau (Sec. 2.3, accuracy and
+cost), the identities chi = [H^{-1}]_{11} = 1/(1-r) >= 1, chi <= cond(H),
+Lambda <= sqrt(chi) (eq. chi via coupling and the two remarks before it),
+chi_tau = chi_T after the bisection (eq. regularized MLS amplification), the
+Shepard limit tau -> infinity, an independent dense augmented least-squares
+solve (SVD), rotation invariance, brute-force nearest neighbours, and the
+h^{K+1} decay of Theorem 2.1 / Theorem 2.4."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from hamls_synth import SplitMix64, uniform_sphere
+
+LD = O.LD
+
+
+def _rotation(seed):
+    q, _ = np.linalg.qr(np.random.default_rng(seed).standard_normal((3, 3)))
+    return q * np.sign(np.linalg.det(q))
+
+
+def _cap_nodes(q, radius, n, seed, squash=1.0):
+    """n random nodes in the geodesic cap of the given radius around q
+    (optionally squashed along e2 to make the local problem ill-conditioned)."""
+    rng = np.random.default_rng(seed)
+    e1, e2 = (a.astype(float) for a in O.tangent_frame(q.astype(LD)))
+    r = radius * np.sqrt(rng.uniform(0, 1, n)) * 0.999
+    a = rng.uniform(0, 2 * np.pi, n)
+    vec = np.cos(a)[:, None] * e1 + squash * np.sin(a)[:, None] * e2
+    vec /= np.linalg.norm(vec, axis=1, keepdims=True)
+    x = np.cos(r)[:, None] * q[None, :] + np.sin(r)[:, None] * vec
+    return x / np.linalg.norm(x, axis=1, keepdims=True)
+
+
+def _tangent_poly(q, xs, K, seed):
+    rng = np.random.default_rng(seed)
+    e1, e2 = O.tangent_frame(q.astype(LD))
+    u, v = xs.astype(LD) @ e1, xs.astype(LD) @ e2
+    coef = rng.standard_normal(O.dim_tan(K))
+    y = np.zeros(len(xs), dtype=LD)
+    for c, (a, b, _) in zip(coef, O.monomial_exponents(K)):
+        y += LD(c) * u ** a * v ** b
+    return y, coef[0]
+
+
+Q = np.array([0.36, -0.48, 0.8])
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 4])
+def test_reproduces_tangent_polynomials_without_regularisation(K):
+    q = Q / np.linalg.norm(Q)
+    xs = _cap_nodes(q, 0.2, 4 * O.dim_tan(K), seed=K)
+    y, p0 = _tangent_poly(q, xs, K, seed=10 + K)
+    p = O.Params(chi_target=1e300, chi_full=2e300)
+    res = O.mls_at(q.astype(LD), xs, y, LD(0.2), K, p)
+    assert res.tau_tilde == 0
+    assert abs(float(res.c1) - p0) < 1e-13 * (1 + abs(p0))
+
+
+@pytest.mark.parametrize("tau", [0.0, 0.3, 7.0, 1e6])
+def test_reproduces_constants_for_every_tau(tau):
+    q = Q / np.linalg.norm(Q)
+    xs = _cap_nodes(q, 0.1, 30, seed=3)
+    res = O.mls_at(q.astype(LD), xs, np.full(30, 2.5), LD(0.1), 3, O.Params(), tau_override=tau)
+    assert abs(float(res.c1) - 2.5) < 1e-14
+
+
+def test_regularised_does_not_reproduce_linear_in_general():
+    # Sec. 2.3: tau > 0 only guarantees constants
+    q = Q / np.linalg.norm(Q)
+    xs = _cap_nodes(q, 0.1, 30, seed=3)
+    y, p0 = _tangent_poly(q, xs, 1, seed=4)
+    res = O.mls_at(q.astype(LD), xs, y, LD(0.1), 1, O.Params(), tau_override=50.0)
+    assert abs(float(res.c1) - p0) > 1e-6
+
+
+def _chi_identities(res):
+    H = (res.B.T @ res.B).astype(float)
+    Hinv = np.linalg.inv(H)
+    chi = float(res.chi)
+    assert chi >= 1.0
+    assert abs(Hinv[0, 0] - chi) < 1e-9 * chi
+    ev = np.linalg.eigvalsh(H)
+    assert chi <= ev[-1] / ev[0] * (1 + 1e-9)
+    assert chi <= 1 / ev[0] * (1 + 1e-9)
+    # Lebesgue constant Lambda = sum_i |sqrt(w_i) psi_i|, psi = B H^{-1} e1
+    psi = res.B.astype(float) @ Hinv[:, 0]
+    lam = np.sum(np.sqrt(res.wn.astype(float)) * np.abs(psi))
+    assert lam <= math.sqrt(chi) * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("squash,seed", [(1.0, 1), (0.3, 2), (0.05, 3)])
+def test_chi_identities(squash, seed):
+    q = Q / np.linalg.norm(Q)
+    xs = _cap_nodes(q, 0.15, 40, seed=seed, squash=squash)
+    res = O.mls_at(q.astype(LD), xs, np.random.default_rng(seed).standard_normal(40), LD(0.15), 3, O.Params())
+    _chi_identities(res)
+
+
+def _one_sided(q, n, seed, K=3):
+    """Local nodes clustered on one side of q: large centre amplification."""
+    rng = np.random.default_rng(seed)
+    e1, e2 = (a.astype(float) for a in O.tangent_frame(q.astype(LD)))
+    r = rng.uniform(0.6, 0.95, n) * 0.1
+    a = rng.uniform(-0.6, 0.6, n)
+    vec = np.cos(a)[:, None] * e1 + np.sin(a)[:, None] * e2
+    x = np.cos(r)[:, None] * q[None, :] + np.sin(r)[:, None] * vec
+    return x / np.linalg.norm(x, axis=1, keepdims=True)
+
+
+def test_bisection_hits_chi_target():
+    q = Q / np.linalg.norm(Q)
+    xs = _one_sided(q, 60, 5)
+    y = np.random.default_rng(5).standard_normal(60)
+    p = O.Params()
+    res = O.mls_at(q.astype(LD), xs, y, LD(0.1), 3, p)
+    assert res.chi > p.chi_full                  # fully regularised case
+    assert res.tau_tilde == res.tau > 0
+    r_tau = np.sum(res.d * res.d / (1 + res.tau * res.mu))
+    assert abs(float(1 / (1 - r_tau)) - p.chi_target) < 1e-12 * p.chi_target
+    # chi_tau = [H_tau^{-1}]_{11} with C replaced by C_tau = L (I + tau D) L^T
+    H = (res.B.T @ res.B)
+    Ht = H.copy()
+    Ht[1:, 1:] = res.L @ np.diag(1 + res.tau * res.mu) @ res.L.T
+    assert abs(np.linalg.inv(Ht.astype(float))[0, 0] - p.chi_target) < 1e-8 * p.chi_target
+    _chi_identities(res)
+
+
+def test_r_tau_monotone_decreasing():
+    q = Q / np.linalg.norm(Q)
+    res = O.mls_at(q.astype(LD), _one_sided(q, 60, 6), np.zeros(60), LD(0.1), 3, O.Params())
+    taus = np.geomspace(1e-6, 1e6, 200).astype(LD)
+    r = np.array([np.sum(res.d * res.d / (1 + t * res.mu)) for t in taus])
+    assert np.all(np.diff(r.astype(float)) < 0) and r[-1] < 1e-5
+
+
+@pytest.mark.parametrize("tau", [0.0, 0.01, 3.0])
+def test_closed_form_equals_normal_equations(tau):
+    q = Q / np.linalg.norm(Q)
+    xs = _one_sided(q, 50, 7)
+    y = np.random.default_rng(7).standard_normal(50)
+    res = O.mls_at(q.astype(LD), xs, y, LD(0.1), 3, O.Params(), tau_override=tau)
+    assert abs(float(res.c1) - float(O.solve_local_literal(res))) < 1e-10 * (1 + abs(float(res.c1)))
+
+
+@pytest.mark.parametrize("tau", [0.0, 0.05, 2.0])
+def test_against_dense_augmented_lsq(tau):
+    # min || [B; sqrt(tau) [0 | D^{1/2} L^T]] c - [y_w; 0] ||, solved by SVD
+    q = Q / np.linalg.norm(Q)
+    xs = _one_sided(q, 45, 8)
+    y = np.random.default_rng(8).standard_normal(45)
+    res = O.mls_at(q.astype(LD), xs, y, LD(0.1), 3, O.Params(), tau_override=tau)
+    B = res.B.astype(float)
+    m = B.shape[1]
+    R = np.zeros((m - 1, m))
+    R[:, 1:] = np.sqrt(tau) * np.diag(np.sqrt(res.mu.astype(float))) @ res.L.astype(float).T
+    A = np.vstack([B, R])
+    rhs = np.concatenate([res.yw.astype(float), np.zeros(m - 1)])
+    c = np.linalg.lstsq(A, rhs, rcond=None)[0]
+    assert abs(c[0] - float(res.c1)) < 1e-9 * (1 + abs(c[0]))
+
+
+def test_shepard_limit():
+    # tau -> infinity: the centre value tends to the weighted mean sum w_i y_i
+    q = Q / np.linalg.norm(Q)
+    xs = _one_sided(q, 40, 9)
+    y = np.random.default_rng(9).standard_normal(40)
+    res = O.mls_at(q.astype(LD), xs, y, LD(0.1), 3, O.Params(), tau_override=1e14)
+    assert abs(float(res.c1) - float(np.sum(res.wn * y))) < 1e-10
+
+
+def test_rotation_invariance():
+    q = Q / np.linalg.norm(Q)
+    xs = _one_sided(q, 50, 11)
+    y = np.random.default_rng(11).standard_normal(50)
+    p = O.Params()
+    a = O.mls_at(q.astype(LD), xs, y, LD(0.1), 3, p)
+    R = _rotation(3)
+    b = O.mls_at((R @ q).astype(LD), xs @ R.T, y, LD(0.1), 3, p)
+    assert abs(float(a.c1 - b.c1)) < 1e-12 and abs(float(a.chi - b.chi)) < 1e-9 * float(a.chi)
+    # rotating only the tangent frame leaves the ansatz space, and c1, unchanged
+    e1, e2 = O.tangent_frame(q.astype(LD))
+    ang = LD(0.7)
+    f = (np.cos(ang) * e1 + np.sin(ang) * e2, -np.sin(ang) * e1 + np.cos(ang) * e2)
+    c = O.mls_at(q.astype(LD), xs, y, LD(0.1), 3, p, frame=f)
+    assert abs(float(a.c1 - c.c1)) < 1e-12 and abs(float(a.tau_tilde - c.tau_tilde)) < 1e-9 * (1 + float(a.tau))
+
+
+def test_smoothstep_is_c3():
+    # tau~ must be C^3 across chi_T and chi_full (Sec. 2.3): the blend S has
+    # S(0) = 0, S(1) = 1 and vanishing derivatives of order 1..3 at both ends.
+    S = O.smoothstep3
+    ts = np.linspace(0, 1, 12)
+    poly = np.polynomial.Polynomial.fit(ts, S(ts), 7).convert()
+    for t0, v0 in ((0.0, 0.0), (1.0, 1.0)):
+        assert abs(poly(t0) - v0) < 1e-12
+        for k in (1, 2, 3):
+            assert abs(poly.deriv(k)(t0)) < 1e-8
+    assert abs(poly.deriv(4)(0.0)) > 1            # not C^4-flat: a genuine blend
+    assert np.all(np.diff(S(np.linspace(0, 1, 101))) >= 0)
+
+
+def test_wendland_shape():
+    r = np.linspace(0, 1.2, 121)
+    w = O.wendland(r)
+    assert w[0] == 3 and np.all(w[r >= 1] == 0) and np.all(np.diff(w) <= 0)
+    # C^4 at r = 1: the first four one-sided derivatives vanish
+    for k in range(1, 5):
+        h = 1e-3
+        pts = [O.wendland(np.array(1.0 - i * h)) for i in range(k + 1)]
+        assert abs(sum((-1) ** i * math.comb(k, i) * pts[i] for i in range(k + 1)) / h ** k) < 1e5 * h ** (6 - k)
+
+
+def test_knn_brute_force():
+    x = uniform_sphere(SplitMix64(5), 700)
+    q = uniform_sphere(SplitMix64(6), 50)
+    ns = O.NodeSet(x)
+    for n in (1, 7, 24):
+        got = ns.knn_chord2(q, n)
+        c2 = O.chord2(q[:, None, :], x[None, :, :])
+        exp = np.sort(c2, axis=1)[:, n - 1]
+        assert np.array_equal(got, exp)
+
+
+def test_ball_brute_force():
+    x = uniform_sphere(SplitMix64(7), 900)
+    ns = O.NodeSet(x)
+    for j, q in enumerate(uniform_sphere(SplitMix64(8), 20)):
+        rho2 = 0.02 + 0.01 * j
+        exp = np.nonzero(O.chord2(q[None, :], x) < rho2)[0]
+        assert np.array_equal(ns.ball(q, rho2), exp)
+
+
+def test_shepard_reproduces_constants():
+    aux = O.fibonacci_points(2000)
+    from scipy.spatial import cKDTree
+    q = uniform_sphere(SplitMix64(9), 30)
+    vals = np.full(2000, 0.123, dtype=LD)
+    out = O.shepard(q, aux, cKDTree(aux), vals, 3 * math.sqrt(4 * math.pi / 2000))
+    assert np.allclose(out.astype(float), 0.123, rtol=1e-15)
+
+
+def test_fibonacci_grid_nearly_uniform():
+    aux = O.fibonacci_points(5000)
+    assert np.allclose(np.linalg.norm(aux, axis=1), 1, atol=1e-15)
+    tree_d, _ = __import__("scipy.spatial", fromlist=["cKDTree"]).cKDTree(aux).query(uniform_sphere(SplitMix64(1), 2000))
+    assert tree_d.max() < 1.2 * math.sqrt(4 * math.pi / 5000)
+
+
+def test_support_radius_holds_n_nodes_and_guard():
+    x = uniform_sphere(SplitMix64(21), 3000)
+    g = O.quad_grid(8)
+    p = O.Params()
+    sup = O.support_radius(O.NodeSet(x), g.xyz, 2, p)
+    assert np.all(sup.count >= O.dim_tan(2))
+    # paper: (1 + eps) d~_n > d_n for a fine auxiliary grid, hence about n nodes
+    assert np.median(sup.count) >= p.n_for(2) * 0.9
+    # a hole smoothed over a very wide Shepard radius: inside the hole the
+    # smoothed radius is far too small, so the guard must take over there
+    from hamls_synth import remove_caps
+    x2 = remove_caps(uniform_sphere(SplitMix64(22), 4000), np.array([[0.0, 0.6, 0.8]]), np.array([0.45]))
+    sup2 = O.support_radius(O.NodeSet(x2), g.xyz, 2, O.Params(aux_points=200, aux_radius=6.0))
+    assert np.all(sup2.count >= O.dim_tan(2))
+    assert sup2.guarded.any()
+
+
+def _fibonacci_nodes(M):
+    return O.fibonacci_points(M)
+
+
+@pytest.mark.parametrize("K", [2, 3])
+def test_error_decays_like_h_to_k_plus_1(K):
+    # Theorem 2.1 (good data): |M f - f| <= C h^{K+1}; unregularised MLS on
+    # Fibonacci nodes, smooth f, the max error at the grid nodes of N = 8.
+    c = np.array([0.2, 0.3, 0.93])
+    c /= np.linalg.norm(c)
+    g = O.quad_grid(8)
+    exact = np.exp(-np.sum((g.xyz - c) ** 2, axis=1) / 0.5)
+    p = O.Params(chi_target=1e300, chi_full=2e300)
+    Ms = [2000, 8000, 32000]
+    errs = []
+    for M in Ms:
+        x = _fibonacci_nodes(M)
+        y = np.exp(-np.sum((x - c) ** 2, axis=1) / 0.5)
+        f, *_ = O.mls_grid_values(x, y, 8, K, p, grid=g)
+        errs.append(np.max(np.abs(f.astype(float) - exact)))
+    h = np.sqrt(4 * np.pi / np.array(Ms))
+    slope = np.polyfit(np.log(h), np.log(errs), 1)[0]
+    assert slope > K + 1 - 0.4, (errs, slope)
+
+
+def test_cell_keys_invariants():
+    x = uniform_sphere(SplitMix64(31), 20000)
+    x[:4] = [[0, 0, 1], [0, 0, -1], [1, 0, 0], [-1, 0, 0]]
+    bands, cells = 64, 128
+    k = O.cell_keys(x, bands, cells)
+    assert k.min() >= 0 and k.max() < bands * cells
+    band, cell = k // cells, k % cells
+    # band is monotone in z, cell is monotone in longitude inside [0, 2 pi)
+    oz = np.argsort(x[:, 2], kind="stable")
+    assert np.all(np.diff(band[oz]) >= 0)
+    ph = np.mod(np.arctan2(x[:, 1], x[:, 0]), 2 * np.pi)
+    op = np.argsort(ph, kind="stable")
+    assert np.all(np.diff(cell[op]) >= 0)
+    # the bands are equal steps of zeta = sign(z)(1 - sqrt(1 - |z|))
+    zeta = np.sign(x[:, 2]) * (1 - np.sqrt(1 - np.abs(x[:, 2])))
+    lo = -1 + 2 * band / bands
+    assert np.all(zeta >= lo - 1e-15) and np.all(zeta <= lo + 2 / bands + 1e-15)
+    perm, sk, start = O.cell_sort(k, bands * cells)
+    assert np.all(np.diff(sk) >= 0)
+    same = sk[1:] == sk[:-1]
+    assert np.all(perm[1:][same] > perm[:-1][same])            # stable
+    assert start[0] == 0 and start[-1] == len(x)
+    cnt = np.bincount(k, minlength=bands * cells)
+    assert np.array_equal(np.diff(start), cnt)
