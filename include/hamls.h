@@ -1,0 +1,166 @@
+/*
+ * hamls.h - C ABI of the B300 (sm_103a) HAMLS library: harmonic approximation
+ * of scattered data on the sphere S^2 via moving least squares.
+ *
+ * The library computes Algorithm 1 of the paper ("Harmonic Approximation via
+ * Moving Least Squares", Sec. 2):
+ *   step 1  a product quadrature grid: Gauss-Legendre nodes t_k = cos(theta_k)
+ *           (k = 0..N, north first) times phi_j = 2 pi j / (2N+2)
+ *           (j = 0..2N+1); M_Q = (N+1)(2N+2) nodes, exact on Pi_{2N} (Sec. 2.1);
+ *   step 2  the regularised MLS value f_j = M_y(q_j) at every grid node
+ *           (Sec. 2.2, 2.3): support radius delta(q) = (1+eps) d~_n(q)
+ *           (eq. adaptive_support_radius, smoothed over a Fibonacci auxiliary
+ *           grid), Wendland weights (eq. weight_function_radial), tangent-plane
+ *           polynomials of degree <= K, centre amplification chi
+ *           (eq. chi via coupling), degree-adapted regularisation tau found by
+ *           bisection (eq. regularized MLS amplification), smoothed tau~;
+ *   step 3  the adjoint transform fhat = F^H W f on the grid: a DFT over
+ *           every ring, then the associated-Legendre quadrature
+ *           (eq. quadrature_based_approximation).
+ *
+ * Notation: N is the harmonic bandwidth (the paper's L), M the number of
+ * scattered nodes (the paper's N), K the MLS degree, m = (K+1)(K+2)/2.
+ *
+ * Memory and ownership. Every pointer argument may be a device pointer or a
+ * host pointer (pageable or pinned); the library detects which with
+ * cudaPointerGetAttributes and stages host data through buffers the plan owns.
+ * The caller owns all argument buffers; the plan owns every device allocation
+ * it makes (all of them inside hamls_plan, none in hamls_replan/hamls_fit).
+ * Calls are stream-ordered and asynchronous: inputs must stay valid, and
+ * outputs must not be read, until the stream work is done (hamls_sync).
+ * A plan must not be used from two streams at once.
+ *
+ * Errors. No exception crosses the ABI and the library never aborts the
+ * process. Argument errors are returned immediately. Conditions found on the
+ * device (too few nodes in a support, support radius >= pi/2, non-finite
+ * values, nodes off the unit sphere) are recorded in a device status word and
+ * returned by hamls_sync.
+ */
+#ifndef HAMLS_H
+#define HAMLS_H
+
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hamls_plan_s* hamls_plan_t;
+
+typedef enum {
+  HAMLS_OK = 0,
+  HAMLS_ERR_INVALID_ARG = 1,        /* bad argument, or a node not on the unit sphere */
+  HAMLS_ERR_OOM = 2,                /* a device allocation failed (plan creation only) */
+  HAMLS_ERR_CUDA = 3,               /* a CUDA runtime call failed */
+  HAMLS_ERR_UNDERDETERMINED = 4,    /* fewer than m nodes in a support even after the guard */
+  HAMLS_ERR_SUPPORT_TOO_LARGE = 5,  /* delta(q) >= pi/2: no open hemisphere (Sec. 2.3) */
+  HAMLS_ERR_TIMEOUT = 6,            /* hamls_sync gave up waiting */
+  HAMLS_ERR_NONFINITE = 7,          /* a value or node coordinate is NaN/Inf */
+  HAMLS_ERR_CAPACITY = 8            /* M exceeds the plan's capacity */
+} hamls_status;
+
+typedef enum { HAMLS_FP64 = 0, HAMLS_MIXED = 1 } hamls_precision;
+
+/* Method parameters. hamls_default_params fills the defaults given here. */
+typedef struct {
+  int     n_target;     /* target neighbour count n; 0 => 4 m (Sec. 3.2, n = 4 dim Pi_K^tan) */
+  double  eps;          /* delta = (1+eps) d~_n (eq. adaptive_support_radius); default 0.05 */
+  double  chi_target;   /* chi_T > 1 (Sec. 2.3, choosing the regularization strength); default 16 */
+  double  chi_full;     /* chi_full > chi_T, full regularisation from here on; default 32 */
+  double  sobolev_s;    /* s in mu_j = (l(j)(l(j)+1))^s (eq. mls degree multipliers); default 1 */
+  int64_t aux_points;   /* Fibonacci auxiliary grid size; 0 => 2 M_Q (Sec. 2.2, last paragraph) */
+  double  aux_radius;   /* Shepard support radius in units of sqrt(4 pi / aux_points); default 3 */
+  double  pivot_floor;  /* squared Cholesky pivot at or below which a direction is dropped; 1e-12 */
+  int     precision;    /* hamls_precision; default HAMLS_FP64 */
+  double  fp64_pivot;   /* MIXED only: squared FP32 pivot below which the local Cholesky is
+                           redone in FP64; default 1e-4 */
+} hamls_params;
+
+/* Per-plan statistics of the last plan/replan and fit. */
+typedef struct {
+  int64_t sum_n;          /* sum over grid nodes of n(q) = #X(q) (eq. number_of_local_nodes) */
+  int64_t min_n, max_n;
+  int64_t n_regularized;  /* grid nodes with tau~ > 0 */
+  int64_t n_guarded;      /* grid nodes whose support came from the exact-d_n guard */
+  int64_t n_fp64_redo;    /* MIXED: grid nodes whose local solve ran in FP64 */
+  int64_t n_dropped;      /* basis directions dropped by the pivot floor, summed */
+  int64_t grid_nodes;     /* M_Q */
+  int64_t aux_points;     /* size of the auxiliary grid */
+  int32_t bands, cells;   /* neighbour structure: latitude bands and cells per band */
+} hamls_fit_stats;
+
+/* Fill *p with the defaults listed in hamls_params. */
+void hamls_default_params(hamls_params* p);
+
+/*
+ * hamls_plan - allocate a plan for up to M nodes at bandwidth N and degree K
+ * and build everything that depends on the nodes only: the quadrature grid
+ * (Sec. 2.1), the cell list over the nodes, d_n on the auxiliary grid,
+ * delta(q) and n(q) at every grid node (Sec. 2.2).
+ *   out          receives the plan handle (NULL on failure)
+ *   nodes_xyz    M x 3 doubles, row-major unit vectors x_i (host or device)
+ *   node_weights M doubles v_i > 0 multiplying the MLS weights, e.g. Voronoi
+ *                areas (Sec. 2.2, after Theorem 2.1); NULL means v_i = 1
+ *   M            number of nodes, m <= M < 2^31
+ *   N            bandwidth, 1 <= N <= 1024
+ *   K            MLS degree, 1 <= K <= 4
+ *   p            parameters, NULL for the defaults
+ *   stream       CUDA stream for all work (0 = legacy default stream)
+ * Returns HAMLS_OK, HAMLS_ERR_INVALID_ARG, HAMLS_ERR_OOM or HAMLS_ERR_CUDA.
+ */
+hamls_status hamls_plan(hamls_plan_t* out, const double* nodes_xyz, const double* node_weights,
+                        int64_t M, int N, int K, const hamls_params* p, cudaStream_t stream);
+
+/*
+ * hamls_replan - rebuild the node-dependent part of an existing plan for a new
+ * node set of M' <= M (the plan's capacity) nodes, with no allocation.
+ * Arguments as in hamls_plan. Returns HAMLS_ERR_CAPACITY if M' is too large.
+ */
+hamls_status hamls_replan(hamls_plan_t plan, const double* nodes_xyz, const double* node_weights,
+                          int64_t M, cudaStream_t stream);
+
+/*
+ * hamls_fit - Algorithm 1 steps 2 and 3 for one set of values at the plan's nodes.
+ *   values  M doubles y_i (host or device)
+ *   coeffs  (N+1)(N+2)/2 complex coefficients, interleaved (re, im) doubles,
+ *           packed m-major: order m = 0..N starts at m(N+1) - m(m-1)/2 and
+ *           holds l = m..N. Fully normalised complex spherical harmonics with
+ *           the Condon-Shortley phase; for real data fhat_l^{-m} =
+ *           (-1)^m conj(fhat_l^m) gives the negative orders.
+ * Complex data (the paper allows y in C) is two calls, one per part.
+ */
+hamls_status hamls_fit(hamls_plan_t plan, const double* values, double* coeffs, cudaStream_t stream);
+
+/* Wait (at most timeout_ms, < 0 = forever) for the plan's stream work and
+ * return the first device-detected error, or HAMLS_OK. Clears the status. */
+hamls_status hamls_sync(hamls_plan_t plan, int timeout_ms);
+
+/* Statistics of the last plan/replan and fit (synchronises the stream). */
+hamls_status hamls_stats(hamls_plan_t plan, hamls_fit_stats* out);
+
+/* Release every resource of the plan (synchronises its last stream). */
+hamls_status hamls_destroy(hamls_plan_t plan);
+
+/* Static text for a status code. */
+const char* hamls_status_string(hamls_status s);
+
+/*
+ * Stage timing. When enabled, hamls_replan and hamls_fit record CUDA events
+ * around each stage on the caller's stream; hamls_stage_times returns the
+ * elapsed milliseconds of the last call of each stage (synchronises):
+ *   0 cell keys + sort + ranges, 1 auxiliary kNN, 2 Shepard + support radius,
+ *   3 neighbour counts + guard + ordering, 4 value staging, 5 MLS,
+ *   6 ring FFT, 7 Legendre quadrature.  n_out receives the count (8).
+ */
+hamls_status hamls_set_timing(hamls_plan_t plan, int enable);
+hamls_status hamls_stage_times(hamls_plan_t plan, float* ms, int capacity, int* n_out);
+
+/* Number of kernel launches the library made on the plan's behalf since the
+ * last reset (reset with reset != 0). */
+int64_t hamls_launch_count(hamls_plan_t plan, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HAMLS_H */

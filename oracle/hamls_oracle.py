@@ -146,13 +146,20 @@ def quad_grid(N: int) -> Grid:
     return Grid(N, t, w, phi, xyz_ld.astype(np.float64), xyz_ld)
 
 
+GOLDEN_FRAC_Q64 = 0x61C8864680B583EA   # floor(2^64 (3 - sqrt 5)/2), i.e. 1 - 1/Phi in 0.64 fixed point
+
+
 def fibonacci_points(M_aux: int) -> np.ndarray:
-    """Fibonacci (golden-angle spiral) grid, approximately uniform on S^2:
-    z_i = 1 - (2i+1)/M_aux, phi_i = i * 2 pi (1 - 1/Phi)."""
-    i = np.arange(M_aux, dtype=LD)
-    z = 1 - (2 * i + 1) / LD(M_aux)
-    golden = 2 * PI_LD * (1 - 1 / ((1 + np.sqrt(LD(5))) / 2))
-    ph = np.fmod(i * golden, 2 * PI_LD)
+    """Fibonacci (golden-angle spiral) grid, approximately uniform on S^2
+    (Sec. 2.2 names it for the auxiliary grid): z_i = 1 - (2i+1)/M_aux,
+    phi_i = 2 pi {i (1 - 1/Phi)}. The fractional part is taken in 64-bit
+    fixed point and truncated to 53 bits, so that it is exact for any i."""
+    i = np.arange(M_aux, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        fr = (i * np.uint64(GOLDEN_FRAC_Q64)) >> np.uint64(11)
+    frac = fr.astype(LD) / LD(2.0 ** 53)
+    z = 1 - (2 * i.astype(LD) + 1) / LD(M_aux)
+    ph = 2 * PI_LD * frac
     s = np.sqrt(1 - z * z)
     return np.stack([s * np.cos(ph), s * np.sin(ph), z], axis=1).astype(np.float64)
 
@@ -366,7 +373,8 @@ def local_design(q_ld, xs, delta, vs, K, frame=None):
     ex = monomial_exponents(K)
     G = np.stack([u ** a * v ** b for (a, b, _) in ex], axis=1)
     scale = np.sqrt(np.sum(wn[:, None] * G * G, axis=0))
-    B = np.sqrt(wn)[:, None] * G / scale[None, :]
+    inv = np.where(scale > 0, 1 / np.where(scale > 0, scale, 1), 0)   # a zero column stays zero (dropped)
+    B = np.sqrt(wn)[:, None] * G * inv[None, :]
     degrees = np.array([k for (_, _, k) in ex])
     return B, wn, degrees
 

@@ -1,0 +1,728 @@
+// api.cu - the C ABI of the HAMLS library (include/hamls.h, include/hamls_debug.h).
+//
+// A plan owns one device arena sized at creation for its capacity M, its
+// bandwidth N and degree K; hamls_replan and hamls_fit never allocate. Every
+// stage runs on the caller's stream; the host is never consulted in between.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <thread>
+#include "../../include/hamls.h"
+#include "../../include/hamls_debug.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace hamls;
+
+static int dim_tan_host(int K) { return (K + 1) * (K + 2) / 2; }
+
+namespace {
+
+constexpr int NSTAGE = 8;
+
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0, cap = 0;
+  template <typename T>
+  T* take(size_t count) {
+    size_t bytes = ((count * sizeof(T)) + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+int key_bands(int64_t M) {
+  int b = 16;
+  while ((int64_t)b * b * 4 < M && b < 4096) b *= 2;
+  return b;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+__global__ void reset_status_kernel(DevStatus* st, int full) {
+  if (threadIdx.x == 0) {
+    if (full) {
+      st->flags = 0;
+      for (int i = 0; i < 16; ++i) st->cnt[i] = 0;
+      st->cnt[C_MIN_N] = ~0ull;
+    } else {
+      st->cnt[C_REG] = st->cnt[C_REDO] = st->cnt[C_DROP] = st->cnt[C_BATCH] = st->cnt[C_REDO_LIST] = 0;
+    }
+  }
+}
+
+}  // namespace
+
+struct hamls_plan_s {
+  int device = 0, num_sms = 148;
+  int64_t Mcap = 0, M = 0;
+  int N = 0, K = 0, m = 0, n_target = 0, MQ = 0, L = 0, M_aux = 0;
+  hamls_params p;
+  bool mixed = false, has_weights = false;
+  Arena arena;
+  GridTables g;
+  // scattered nodes
+  int B = 0, P = 0;
+  uint32_t *keys, *vals, *keys_alt, *vals_alt, *counts, *start;
+  const uint32_t *perm = nullptr, *skeys = nullptr;
+  double *px, *py, *pz, *sw, *sy;
+  float4* pf;
+  float* swf;
+  // auxiliary grid
+  int aB = 0, aP = 0;
+  uint32_t *akeys, *avals, *akeys_alt, *avals_alt, *astart;
+  const uint32_t *aperm = nullptr, *askeys = nullptr;
+  double *ax, *ay, *az, *apx, *apy, *apz, *dn_aux;
+  float4* apf;
+  // grid nodes
+  double *delta, *rho2, *fgrid, *chi, *tau;
+  int32_t* count;
+  uint8_t* guarded;
+  uint32_t *guard_list, *okeys, *ovals, *okeys_alt, *ovals_alt;
+  const uint32_t* order = nullptr;
+  float* redo_mom;
+  uint32_t* redo_node;
+  void* F;
+  double* coeffs;
+  // staging of host inputs
+  double *in_nodes, *in_wts, *in_vals;
+  DevStatus* st;
+  DevStatus* st_host = nullptr;
+  bool timing = false;
+  cudaEvent_t ev[NSTAGE][2];
+  bool ev_made = false;
+  bool ev_used[NSTAGE];
+  cudaStream_t last = 0;
+  int64_t launches = 0;
+  int radices[32];
+  int nrad = 0;
+};
+
+namespace {
+
+hamls_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return HAMLS_OK;
+  if (e == cudaErrorMemoryAllocation) return HAMLS_ERR_OOM;
+  return HAMLS_ERR_CUDA;
+}
+
+#define HAMLS_TRY(expr)                              \
+  do {                                               \
+    cudaError_t _e = (expr);                         \
+    if (_e != cudaSuccess) return cuda_status(_e);   \
+  } while (0)
+
+void carve(hamls_plan_s* P) {
+  Arena& A = P->arena;
+  A.off = 0;
+  const int64_t M = P->Mcap;
+  const int N = P->N, L = P->L, MQ = P->MQ, Ma = P->M_aux;
+  const size_t ncoef = (size_t)(N + 1) * (N + 2) / 2;
+  const int sortmax = (int)std::max<int64_t>(std::max<int64_t>(M, Ma), MQ);
+  // grid tables
+  P->g.t = A.take<double>(N + 1);
+  P->g.w = A.take<double>(N + 1);
+  P->g.s = A.take<double>(N + 1);
+  P->g.cphi = A.take<double>(L);
+  P->g.sphi = A.take<double>(L);
+  P->g.a_rec = A.take<double>(ncoef);
+  P->g.b_rec = A.take<double>(ncoef);
+  P->g.A64 = P->mixed ? nullptr : A.take<double>(ncoef * P->g.hc);
+  P->g.A32 = P->mixed ? A.take<float>(ncoef * P->g.hc) : nullptr;
+  P->g.W64 = A.take<double2>(L);
+  P->g.W32 = A.take<float2>(L);
+  // nodes
+  P->keys = A.take<uint32_t>(M);
+  P->vals = A.take<uint32_t>(M);
+  P->keys_alt = A.take<uint32_t>(M);
+  P->vals_alt = A.take<uint32_t>(M);
+  P->counts = A.take<uint32_t>((size_t)256 * radix_blocks(sortmax));
+  P->start = A.take<uint32_t>((size_t)P->B * P->P + 1);
+  P->px = A.take<double>(M);
+  P->py = A.take<double>(M);
+  P->pz = A.take<double>(M);
+  P->sy = A.take<double>(M);
+  P->sw = A.take<double>(M);
+  P->pf = A.take<float4>(M);
+  P->swf = A.take<float>(M);
+  // aux
+  P->akeys = A.take<uint32_t>(Ma);
+  P->avals = A.take<uint32_t>(Ma);
+  P->akeys_alt = A.take<uint32_t>(Ma);
+  P->avals_alt = A.take<uint32_t>(Ma);
+  P->astart = A.take<uint32_t>((size_t)P->aB * P->aP + 1);
+  P->ax = A.take<double>(Ma);
+  P->ay = A.take<double>(Ma);
+  P->az = A.take<double>(Ma);
+  P->apx = A.take<double>(Ma);
+  P->apy = A.take<double>(Ma);
+  P->apz = A.take<double>(Ma);
+  P->dn_aux = A.take<double>(Ma);
+  P->apf = A.take<float4>(Ma);
+  // grid nodes
+  P->delta = A.take<double>(MQ);
+  P->rho2 = A.take<double>(MQ);
+  P->fgrid = A.take<double>(MQ);
+  P->chi = A.take<double>(MQ);
+  P->tau = A.take<double>(MQ);
+  P->count = A.take<int32_t>(MQ);
+  P->guarded = A.take<uint8_t>(MQ);
+  P->guard_list = A.take<uint32_t>(MQ);
+  P->okeys = A.take<uint32_t>(MQ);
+  P->ovals = A.take<uint32_t>(MQ);
+  P->okeys_alt = A.take<uint32_t>(MQ);
+  P->ovals_alt = A.take<uint32_t>(MQ);
+  const int NV = dim_tan_host(2 * P->K) + dim_tan_host(P->K);
+  P->redo_mom = P->mixed ? A.take<float>((size_t)MQ * NV) : nullptr;
+  P->redo_node = A.take<uint32_t>(MQ);
+  P->F = A.take<double2>((size_t)(N + 1) * (N + 1));
+  P->coeffs = A.take<double>(2 * ncoef);
+  P->in_nodes = A.take<double>((size_t)3 * M);
+  P->in_wts = A.take<double>(M);
+  P->in_vals = A.take<double>(M);
+  P->st = A.take<DevStatus>(1);
+}
+
+Cells node_cells(const hamls_plan_s* P) {
+  Cells c;
+  c.B = P->B;
+  c.P = P->P;
+  c.n = (int)P->M;
+  c.start = P->start;
+  c.pf = P->pf;
+  c.px = P->px;
+  c.py = P->py;
+  c.pz = P->pz;
+  c.perm = P->perm;
+  return c;
+}
+
+Cells aux_cells(const hamls_plan_s* P) {
+  Cells c;
+  c.B = P->aB;
+  c.P = P->aP;
+  c.n = P->M_aux;
+  c.start = P->astart;
+  c.pf = P->apf;
+  c.px = P->apx;
+  c.py = P->apy;
+  c.pz = P->apz;
+  c.perm = P->aperm;
+  return c;
+}
+
+void stage_begin(hamls_plan_s* P, int i, cudaStream_t s) {
+  if (P->timing) {
+    cudaEventRecord(P->ev[i][0], s);
+    P->ev_used[i] = true;
+  }
+}
+void stage_end(hamls_plan_s* P, int i, cudaStream_t s) {
+  if (P->timing) cudaEventRecord(P->ev[i][1], s);
+}
+
+SupportArgs support_args(hamls_plan_s* P) {
+  SupportArgs a;
+  a.nodes = node_cells(P);
+  a.aux = aux_cells(P);
+  a.n_target = P->n_target;
+  a.m = P->m;
+  a.N = P->N;
+  a.eps = P->p.eps;
+  a.rho_aux = P->p.aux_radius * sqrt(4.0 * M_PI / (double)P->M_aux);
+  a.ring_t = P->g.t;
+  a.ring_s = P->g.s;
+  a.cphi = P->g.cphi;
+  a.sphi = P->g.sphi;
+  a.dn_aux_sorted = P->dn_aux;
+  a.delta = P->delta;
+  a.rho2 = P->rho2;
+  a.count = P->count;
+  a.guarded = P->guarded;
+  a.guard_list = P->guard_list;
+  a.order_keys = P->okeys;
+  a.order_vals = P->ovals;
+  a.fp64 = P->mixed ? 0 : 1;
+  a.st = P->st;
+  return a;
+}
+
+// node-dependent part of the plan (Sec. 2.2: cell list, d_n, delta, n(q))
+hamls_status build_nodes(hamls_plan_s* P, const double* nodes, const double* wts, int64_t M, cudaStream_t s) {
+  P->M = M;
+  P->has_weights = wts != nullptr;
+  reset_status_kernel<<<1, 32, 0, s>>>(P->st, 1);
+  ++P->launches;
+  const double* dn = nodes;
+  if (!is_device_ptr(nodes)) {
+    HAMLS_TRY(cudaMemcpyAsync(P->in_nodes, nodes, (size_t)M * 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+    dn = P->in_nodes;
+  }
+  const double* dw = wts;
+  if (wts && !is_device_ptr(wts)) {
+    HAMLS_TRY(cudaMemcpyAsync(P->in_wts, wts, (size_t)M * sizeof(double), cudaMemcpyHostToDevice, s));
+    dw = P->in_wts;
+  }
+  stage_begin(P, 0, s);
+  CellBuild cb;
+  memset(&cb, 0, sizeof(cb));
+  cb.n = (int)M;
+  cb.B = P->B;
+  cb.P = P->P;
+  cb.xyz_aos = dn;
+  cb.wts = dw;
+  cb.keys = P->keys;
+  cb.vals = P->vals;
+  cb.keys_alt = P->keys_alt;
+  cb.vals_alt = P->vals_alt;
+  cb.counts = P->counts;
+  cb.start = P->start;
+  cb.px = P->px;
+  cb.py = P->py;
+  cb.pz = P->pz;
+  cb.pf = P->pf;
+  cb.sw = P->sw;
+  cb.swf = P->swf;
+  cb.st = P->st;
+  cb.perm_out = &P->perm;
+  cb.keys_out = &P->skeys;
+  build_cells(cb, s, &P->launches);
+  stage_end(P, 0, s);
+  SupportArgs a = support_args(P);
+  stage_begin(P, 1, s);
+  run_aux_knn(a, s, &P->launches);
+  stage_end(P, 1, s);
+  stage_begin(P, 2, s);
+  run_shepard(a, s, &P->launches);
+  stage_end(P, 2, s);
+  stage_begin(P, 3, s);
+  run_counts(a, s, &P->launches);
+  bool alt = radix_sort_pairs(P->okeys, P->ovals, P->okeys_alt, P->ovals_alt, P->MQ, 20, P->counts, s,
+                              &P->launches);
+  P->order = alt ? P->ovals_alt : P->ovals;
+  stage_end(P, 3, s);
+  P->last = s;
+  return cuda_status(cudaGetLastError());
+}
+
+hamls_status build_static(hamls_plan_s* P, cudaStream_t s) {
+  build_grid_tables(P->g, P->mixed, !P->mixed, s, &P->launches);
+  fibonacci_points(P->ax, P->ay, P->az, P->M_aux, s, &P->launches);
+  CellBuild cb;
+  memset(&cb, 0, sizeof(cb));
+  cb.n = P->M_aux;
+  cb.B = P->aB;
+  cb.P = P->aP;
+  cb.ax = P->ax;
+  cb.ay = P->ay;
+  cb.az = P->az;
+  cb.keys = P->akeys;
+  cb.vals = P->avals;
+  cb.keys_alt = P->akeys_alt;
+  cb.vals_alt = P->avals_alt;
+  cb.counts = P->counts;
+  cb.start = P->astart;
+  cb.px = P->apx;
+  cb.py = P->apy;
+  cb.pz = P->apz;
+  cb.pf = P->apf;
+  cb.st = P->st;
+  cb.perm_out = &P->aperm;
+  cb.keys_out = &P->askeys;
+  build_cells(cb, s, &P->launches);
+  return cuda_status(cudaGetLastError());
+}
+
+bool validate_params(const hamls_params& p) {
+  if (!(p.eps > 0) || !(p.chi_target > 1) || !(p.chi_full > p.chi_target) || !(p.sobolev_s > 0)) return false;
+  if (!(p.aux_radius > 0) || p.aux_points < 0 || !(p.pivot_floor >= 0) || !(p.fp64_pivot >= 0)) return false;
+  if (p.precision != HAMLS_FP64 && p.precision != HAMLS_MIXED) return false;
+  if (p.n_target < 0 || p.n_target > KNN_MAX) return false;
+  return true;
+}
+
+void factor_radices(int L, int* r, int& n) {
+  n = 0;
+  int x = L;
+  for (int p = 2; x > 1; ++p)
+    while (x % p == 0) {
+      r[n++] = p;
+      x /= p;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void hamls_default_params(hamls_params* p) {
+  if (!p) return;
+  p->n_target = 0;
+  p->eps = 0.05;
+  p->chi_target = 16.0;
+  p->chi_full = 32.0;
+  p->sobolev_s = 1.0;
+  p->aux_points = 0;
+  p->aux_radius = 3.0;
+  p->pivot_floor = 1e-12;
+  p->precision = HAMLS_FP64;
+  p->fp64_pivot = 1e-4;
+}
+
+const char* hamls_status_string(hamls_status s) {
+  switch (s) {
+    case HAMLS_OK: return "ok";
+    case HAMLS_ERR_INVALID_ARG: return "invalid argument (or a node not on the unit sphere)";
+    case HAMLS_ERR_OOM: return "device allocation failed";
+    case HAMLS_ERR_CUDA: return "CUDA runtime error";
+    case HAMLS_ERR_UNDERDETERMINED: return "fewer than m nodes in a support after the guard";
+    case HAMLS_ERR_SUPPORT_TOO_LARGE: return "support radius reaches pi/2";
+    case HAMLS_ERR_TIMEOUT: return "timed out waiting for the device";
+    case HAMLS_ERR_NONFINITE: return "non-finite value";
+    case HAMLS_ERR_CAPACITY: return "node count exceeds the plan capacity";
+  }
+  return "unknown status";
+}
+
+hamls_status hamls_plan(hamls_plan_t* out, const double* nodes_xyz, const double* node_weights, int64_t M,
+                        int N, int K, const hamls_params* pin, cudaStream_t stream) {
+  if (!out) return HAMLS_ERR_INVALID_ARG;
+  *out = nullptr;
+  hamls_params p;
+  if (pin) p = *pin;
+  else hamls_default_params(&p);
+  if (!nodes_xyz || K < 1 || K > KMAX || N < 1 || N > 1024 || !validate_params(p)) return HAMLS_ERR_INVALID_ARG;
+  const int m = dim_tan_host(K);
+  const int n_target = p.n_target > 0 ? p.n_target : 4 * m;
+  if (n_target > KNN_MAX || n_target < m) return HAMLS_ERR_INVALID_ARG;
+  if (M < n_target || M >= (int64_t)1 << 31) return HAMLS_ERR_INVALID_ARG;
+  hamls_plan_s* P = new (std::nothrow) hamls_plan_s();
+  if (!P) return HAMLS_ERR_OOM;
+  P->p = p;
+  P->mixed = p.precision == HAMLS_MIXED;
+  P->Mcap = M;
+  P->N = N;
+  P->K = K;
+  P->m = m;
+  P->n_target = n_target;
+  P->L = 2 * N + 2;
+  P->MQ = (N + 1) * P->L;
+  P->M_aux = (int)(p.aux_points > 0 ? p.aux_points : 2 * (int64_t)P->MQ);
+  P->g.N = N;
+  P->g.hc = N / 2 + 1;
+  P->B = key_bands(M);
+  P->P = 2 * P->B;
+  P->aB = key_bands(P->M_aux);
+  P->aP = 2 * P->aB;
+  factor_radices(P->L, P->radices, P->nrad);
+  if (P->nrad > 32) {
+    delete P;
+    return HAMLS_ERR_INVALID_ARG;
+  }
+  cudaGetDevice(&P->device);
+  cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+  carve(P);   // measure
+  P->arena.cap = P->arena.off;
+  cudaError_t e = cudaMalloc((void**)&P->arena.base, P->arena.cap);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete P;
+    return HAMLS_ERR_OOM;
+  }
+  carve(P);   // assign
+  e = cudaMallocHost((void**)&P->st_host, sizeof(DevStatus));
+  if (e != cudaSuccess) {
+    cudaFree(P->arena.base);
+    delete P;
+    return HAMLS_ERR_OOM;
+  }
+  for (int i = 0; i < NSTAGE; ++i) P->ev_used[i] = false;
+  hamls_status s = build_static(P, stream);
+  if (s == HAMLS_OK) s = build_nodes(P, nodes_xyz, node_weights, M, stream);
+  if (s != HAMLS_OK) {
+    hamls_destroy(P);
+    return s;
+  }
+  *out = P;
+  return HAMLS_OK;
+}
+
+hamls_status hamls_replan(hamls_plan_t P, const double* nodes_xyz, const double* node_weights, int64_t M,
+                          cudaStream_t stream) {
+  if (!P || !nodes_xyz) return HAMLS_ERR_INVALID_ARG;
+  if (M > P->Mcap) return HAMLS_ERR_CAPACITY;
+  if (M < P->n_target) return HAMLS_ERR_INVALID_ARG;
+  return build_nodes(P, nodes_xyz, node_weights, M, stream);
+}
+
+hamls_status hamls_fit(hamls_plan_t P, const double* values, double* coeffs, cudaStream_t s) {
+  if (!P || !values || !coeffs) return HAMLS_ERR_INVALID_ARG;
+  reset_status_kernel<<<1, 32, 0, s>>>(P->st, 0);
+  ++P->launches;
+  const double* dv = values;
+  if (!is_device_ptr(values)) {
+    HAMLS_TRY(cudaMemcpyAsync(P->in_vals, values, (size_t)P->M * sizeof(double), cudaMemcpyHostToDevice, s));
+    dv = P->in_vals;
+  }
+  stage_begin(P, 4, s);
+  stage_values(dv, P->perm, (int)P->M, P->sy, P->pf, !P->mixed, P->st, s, &P->launches);
+  stage_end(P, 4, s);
+  MlsArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nodes = node_cells(P);
+  a.sy = P->sy;
+  a.sw = P->has_weights ? P->sw : nullptr;
+  a.swf = P->has_weights ? P->swf : nullptr;
+  a.ring_t = P->g.t;
+  a.ring_s = P->g.s;
+  a.cphi = P->g.cphi;
+  a.sphi = P->g.sphi;
+  a.N = P->N;
+  a.K = P->K;
+  a.delta = P->delta;
+  a.rho2 = P->rho2;
+  a.order = P->order;
+  a.MQ = P->MQ;
+  a.fgrid = P->fgrid;
+  a.chi = P->chi;
+  a.tau = P->tau;
+  a.chiT = P->p.chi_target;
+  a.chiF = P->p.chi_full;
+  a.floor_ = P->p.pivot_floor;
+  a.fp64_pivot = P->p.fp64_pivot;
+  for (int l = 0; l <= KMAX; ++l) a.mu[l] = pow((double)l * (l + 1), P->p.sobolev_s);
+  a.redo_mom = P->redo_mom;
+  a.redo_node = P->redo_node;
+  a.st = P->st;
+  a.num_sms = P->num_sms;
+  stage_begin(P, 5, s);
+  run_mls(a, P->mixed, s, &P->launches);
+  stage_end(P, 5, s);
+  const bool dev_out = is_device_ptr(coeffs);
+  QuadArgs q;
+  memset(&q, 0, sizeof(q));
+  q.g = &P->g;
+  q.fgrid = P->fgrid;
+  q.F = P->F;
+  q.coeffs = dev_out ? coeffs : P->coeffs;
+  for (int i = 0; i < P->nrad; ++i) q.radices[i] = P->radices[i];
+  q.nrad = P->nrad;
+  stage_begin(P, 6, s);
+  run_quadrature(q, P->mixed, s, &P->launches);
+  stage_end(P, 6, s);
+  if (!dev_out) {
+    const size_t ncoef = (size_t)(P->N + 1) * (P->N + 2) / 2;
+    HAMLS_TRY(cudaMemcpyAsync(coeffs, P->coeffs, ncoef * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  P->last = s;
+  return cuda_status(cudaGetLastError());
+}
+
+hamls_status hamls_sync(hamls_plan_t P, int timeout_ms) {
+  if (!P) return HAMLS_ERR_INVALID_ARG;
+  cudaStream_t s = P->last;
+  HAMLS_TRY(cudaMemcpyAsync(P->st_host, P->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(s);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return cuda_status(e);
+    if (timeout_ms >= 0) {
+      auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+      if (ms > timeout_ms) return HAMLS_ERR_TIMEOUT;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  unsigned f = P->st_host->flags;
+  if (f) HAMLS_TRY(cudaMemsetAsync(&P->st->flags, 0, sizeof(unsigned), s));
+  if (f & ST_BADNODE) return HAMLS_ERR_INVALID_ARG;
+  if (f & ST_NONFINITE) return HAMLS_ERR_NONFINITE;
+  if (f & ST_SUPPORT) return HAMLS_ERR_SUPPORT_TOO_LARGE;
+  if (f & (ST_UNDERDET | ST_KNN)) return HAMLS_ERR_UNDERDETERMINED;
+  return HAMLS_OK;
+}
+
+hamls_status hamls_stats(hamls_plan_t P, hamls_fit_stats* out) {
+  if (!P || !out) return HAMLS_ERR_INVALID_ARG;
+  HAMLS_TRY(cudaMemcpyAsync(P->st_host, P->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, P->last));
+  HAMLS_TRY(cudaStreamSynchronize(P->last));
+  const DevStatus& d = *P->st_host;
+  out->sum_n = (int64_t)d.cnt[C_SUM_N];
+  out->min_n = (int64_t)d.cnt[C_MIN_N];
+  out->max_n = (int64_t)d.cnt[C_MAX_N];
+  out->n_regularized = (int64_t)d.cnt[C_REG];
+  out->n_guarded = (int64_t)d.cnt[C_GUARD];
+  out->n_fp64_redo = (int64_t)d.cnt[C_REDO];
+  out->n_dropped = (int64_t)d.cnt[C_DROP];
+  out->grid_nodes = P->MQ;
+  out->aux_points = P->M_aux;
+  out->bands = P->B;
+  out->cells = P->P;
+  return HAMLS_OK;
+}
+
+hamls_status hamls_destroy(hamls_plan_t P) {
+  if (!P) return HAMLS_ERR_INVALID_ARG;
+  cudaStreamSynchronize(P->last);
+  if (P->ev_made)
+    for (int i = 0; i < NSTAGE; ++i) {
+      cudaEventDestroy(P->ev[i][0]);
+      cudaEventDestroy(P->ev[i][1]);
+    }
+  if (P->arena.base) cudaFree(P->arena.base);
+  if (P->st_host) cudaFreeHost(P->st_host);
+  delete P;
+  return HAMLS_OK;
+}
+
+hamls_status hamls_set_timing(hamls_plan_t P, int enable) {
+  if (!P) return HAMLS_ERR_INVALID_ARG;
+  if (enable && !P->ev_made) {
+    for (int i = 0; i < NSTAGE; ++i) {
+      HAMLS_TRY(cudaEventCreate(&P->ev[i][0]));
+      HAMLS_TRY(cudaEventCreate(&P->ev[i][1]));
+    }
+    P->ev_made = true;
+  }
+  P->timing = enable != 0;
+  return HAMLS_OK;
+}
+
+hamls_status hamls_stage_times(hamls_plan_t P, float* ms, int capacity, int* n_out) {
+  if (!P || !ms) return HAMLS_ERR_INVALID_ARG;
+  if (n_out) *n_out = NSTAGE;
+  for (int i = 0; i < NSTAGE && i < capacity; ++i) {
+    ms[i] = -1.f;
+    if (P->ev_made && P->ev_used[i]) {
+      HAMLS_TRY(cudaEventSynchronize(P->ev[i][1]));
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, P->ev[i][0], P->ev[i][1]) == cudaSuccess) ms[i] = t;
+      else cudaGetLastError();
+    }
+  }
+  return HAMLS_OK;
+}
+
+int64_t hamls_launch_count(hamls_plan_t P, int reset) {
+  if (!P) return -1;
+  int64_t v = P->launches;
+  if (reset) P->launches = 0;
+  return v;
+}
+
+// ------------------------------------------------------------------ debug
+static hamls_status copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (!dst) return HAMLS_OK;
+  HAMLS_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+  return HAMLS_OK;
+}
+
+hamls_status hamls_debug_cells(hamls_plan_t P, uint32_t* keys_sorted, uint32_t* perm, uint32_t* cell_start,
+                               cudaStream_t s) {
+  if (!P) return HAMLS_ERR_INVALID_ARG;
+  hamls_status r;
+  if ((r = copy_out(keys_sorted, P->skeys, P->M * 4, s)) != HAMLS_OK) return r;
+  if ((r = copy_out(perm, P->perm, P->M * 4, s)) != HAMLS_OK) return r;
+  if ((r = copy_out(cell_start, P->start, ((size_t)P->B * P->P + 1) * 4, s)) != HAMLS_OK) return r;
+  P->last = s;
+  return HAMLS_OK;
+}
+
+hamls_status hamls_debug_knn(hamls_plan_t P, const double* queries, int64_t nq, int n, double* c2_out,
+                             cudaStream_t s) {
+  if (!P || !queries || !c2_out || n < 1 || n > KNN_MAX || n > P->M || nq < 0) return HAMLS_ERR_INVALID_ARG;
+  if (!is_device_ptr(queries) || !is_device_ptr(c2_out)) return HAMLS_ERR_INVALID_ARG;
+  run_knn_queries(node_cells(P), queries, nq, n, c2_out, P->st, s, &P->launches);
+  P->last = s;
+  return cuda_status(cudaGetLastError());
+}
+
+hamls_status hamls_debug_ball(hamls_plan_t P, const double* queries, const double* rho2, int64_t nq,
+                              int64_t* count, int64_t* idsum, uint64_t* idhash, cudaStream_t s) {
+  if (!P || !queries || !rho2 || !count || !idsum || !idhash || nq < 0) return HAMLS_ERR_INVALID_ARG;
+  if (!is_device_ptr(queries) || !is_device_ptr(rho2) || !is_device_ptr(count) || !is_device_ptr(idsum) ||
+      !is_device_ptr(idhash))
+    return HAMLS_ERR_INVALID_ARG;
+  run_ball_queries(node_cells(P), queries, rho2, nq, count, idsum, idhash, s, &P->launches);
+  P->last = s;
+  return cuda_status(cudaGetLastError());
+}
+
+hamls_status hamls_debug_grid(hamls_plan_t P, double* delta, int32_t* count, double* chi, double* tau_tilde,
+                              double* fgrid, cudaStream_t s) {
+  if (!P) return HAMLS_ERR_INVALID_ARG;
+  const size_t n = P->MQ;
+  hamls_status r;
+  if ((r = copy_out(delta, P->delta, n * 8, s)) != HAMLS_OK) return r;
+  if ((r = copy_out(count, P->count, n * 4, s)) != HAMLS_OK) return r;
+  if ((r = copy_out(chi, P->chi, n * 8, s)) != HAMLS_OK) return r;
+  if ((r = copy_out(tau_tilde, P->tau, n * 8, s)) != HAMLS_OK) return r;
+  if ((r = copy_out(fgrid, P->fgrid, n * 8, s)) != HAMLS_OK) return r;
+  P->last = s;
+  return HAMLS_OK;
+}
+
+__global__ void unsort_aux_kernel(const double* px, const double* py, const double* pz, const double* dn,
+                                  const uint32_t* perm, int n, double* xyz, double* dn_out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t o = perm[i];
+  if (xyz) {
+    xyz[3 * (size_t)o] = px[i];
+    xyz[3 * (size_t)o + 1] = py[i];
+    xyz[3 * (size_t)o + 2] = pz[i];
+  }
+  if (dn_out) dn_out[o] = dn[i];
+}
+
+hamls_status hamls_debug_aux(hamls_plan_t P, double* aux_xyz, double* dn_aux, cudaStream_t s) {
+  if (!P) return HAMLS_ERR_INVALID_ARG;
+  if ((aux_xyz && !is_device_ptr(aux_xyz)) || (dn_aux && !is_device_ptr(dn_aux))) return HAMLS_ERR_INVALID_ARG;
+  unsort_aux_kernel<<<(P->M_aux + 255) / 256, 256, 0, s>>>(P->apx, P->apy, P->apz, P->dn_aux, P->aperm, P->M_aux,
+                                                           aux_xyz, dn_aux);
+  ++P->launches;
+  P->last = s;
+  return cuda_status(cudaGetLastError());
+}
+
+hamls_status hamls_debug_quadrature(hamls_plan_t P, const double* fgrid, double* coeffs, cudaStream_t s) {
+  if (!P || !fgrid || !coeffs) return HAMLS_ERR_INVALID_ARG;
+  if (!is_device_ptr(fgrid) || !is_device_ptr(coeffs)) return HAMLS_ERR_INVALID_ARG;
+  QuadArgs q;
+  memset(&q, 0, sizeof(q));
+  q.g = &P->g;
+  q.fgrid = fgrid;
+  q.F = P->F;
+  q.coeffs = coeffs;
+  for (int i = 0; i < P->nrad; ++i) q.radices[i] = P->radices[i];
+  q.nrad = P->nrad;
+  run_quadrature(q, P->mixed, s, &P->launches);
+  P->last = s;
+  return cuda_status(cudaGetLastError());
+}
+
+hamls_status hamls_debug_gl(hamls_plan_t P, double* t, double* w, cudaStream_t s) {
+  if (!P) return HAMLS_ERR_INVALID_ARG;
+  hamls_status r;
+  if ((r = copy_out(t, P->g.t, (P->N + 1) * 8, s)) != HAMLS_OK) return r;
+  if ((r = copy_out(w, P->g.w, (P->N + 1) * 8, s)) != HAMLS_OK) return r;
+  P->last = s;
+  return HAMLS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,239 @@
+// cells.cu - neighbour structure over a point set on S^2: integer cell keys,
+// a stable LSD radix sort of (key, index), the CSR run table and the sorted
+// FP64/FP32 copies of the points. Everything is bit-exact integer work or
+// exact copies; see common.cuh for the key definition.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace hamls {
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+
+int radix_blocks(int n) { return (n + SORT_TILE - 1) / SORT_TILE; }
+
+// ------------------------------------------------------------- cell keys
+__global__ void keys_kernel(const double* __restrict__ xyz, int n, int B, int P, uint32_t* __restrict__ keys,
+                            uint32_t* __restrict__ idx, DevStatus* st) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x = xyz[3 * (size_t)i], y = xyz[3 * (size_t)i + 1], z = xyz[3 * (size_t)i + 2];
+  double r2 = x * x + y * y + z * z;
+  bool ok = isfinite(x) && isfinite(y) && isfinite(z) && fabs(r2 - 1.0) < 1e-6;
+  if (!ok) {
+    set_flag(st, ST_BADNODE);
+    x = 0.0; y = 0.0; z = 1.0;
+  }
+  keys[i] = cell_key64(x, y, z, B, P);
+  idx[i] = (uint32_t)i;
+}
+
+// points generated on the device (auxiliary grid) are already valid
+__global__ void keys_kernel_soa(const double* __restrict__ px, const double* __restrict__ py,
+                                const double* __restrict__ pz, int n, int B, int P,
+                                uint32_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  keys[i] = cell_key64(px[i], py[i], pz[i], B, P);
+  idx[i] = (uint32_t)i;
+}
+
+// ------------------------------------------------------------ radix sort
+__global__ void __launch_bounds__(SORT_THREADS) radix_hist(const uint32_t* __restrict__ kin, int n, int shift,
+                                                           uint32_t mask, uint32_t* __restrict__ counts,
+                                                           int nblocks) {
+  __shared__ uint32_t h[256];
+  const int tid = threadIdx.x;
+  h[tid] = 0;
+  __syncthreads();
+  const int tile0 = blockIdx.x * SORT_TILE;
+#pragma unroll 4
+  for (int r = 0; r < SORT_ITEMS; ++r) {
+    int i = tile0 + r * SORT_THREADS + tid;
+    if (i < n) atomicAdd(&h[(kin[i] >> shift) & mask], 1u);
+  }
+  __syncthreads();
+  counts[(size_t)tid * nblocks + blockIdx.x] = h[tid];
+}
+
+// exclusive scan of `len` counts in place, one block of 1024 threads
+__global__ void __launch_bounds__(1024) scan_exclusive(uint32_t* __restrict__ a, int len) {
+  __shared__ uint32_t part[1024];
+  const int tid = threadIdx.x;
+  const int per = (len + 1023) / 1024;
+  const int lo = min(tid * per, len), hi = min(lo + per, len);
+  uint32_t s = 0;
+  for (int i = lo; i < hi; ++i) s += a[i];
+  part[tid] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    uint32_t t = tid >= o ? part[tid - o] : 0;
+    __syncthreads();
+    part[tid] += t;
+    __syncthreads();
+  }
+  uint32_t run = part[tid] - s;
+  for (int i = lo; i < hi; ++i) {
+    uint32_t v = a[i];
+    a[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) radix_scatter(const uint32_t* __restrict__ kin,
+                                                              const uint32_t* __restrict__ vin,
+                                                              uint32_t* __restrict__ kout,
+                                                              uint32_t* __restrict__ vout,
+                                                              const uint32_t* __restrict__ offsets, int n,
+                                                              int shift, uint32_t mask, int nblocks) {
+  __shared__ uint32_t warp_cnt[SORT_THREADS / 32][256];
+  __shared__ uint32_t digit_base[256];
+  __shared__ uint32_t blk_off[256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  blk_off[tid] = offsets[(size_t)tid * nblocks + blockIdx.x];
+  digit_base[tid] = 0;
+  const int tile0 = blockIdx.x * SORT_TILE;
+  for (int r = 0; r < SORT_ITEMS; ++r) {
+#pragma unroll
+    for (int w = 0; w < SORT_THREADS / 32; ++w) warp_cnt[w][tid] = 0;
+    __syncthreads();
+    const int i = tile0 + r * SORT_THREADS + tid;
+    const bool ok = i < n;
+    const uint32_t k = ok ? kin[i] : 0u, v = ok ? vin[i] : 0u;
+    const uint32_t d = ok ? ((k >> shift) & mask) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(FULL, d);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (ok && lane == __ffs(peers) - 1) warp_cnt[warp][d] = __popc(peers);
+    __syncthreads();
+    uint32_t run = digit_base[tid];
+#pragma unroll
+    for (int w = 0; w < SORT_THREADS / 32; ++w) {
+      uint32_t c = warp_cnt[w][tid];
+      warp_cnt[w][tid] = run;
+      run += c;
+    }
+    digit_base[tid] = run;
+    __syncthreads();
+    if (ok) {
+      uint32_t pos = blk_off[d] + warp_cnt[warp][d] + (uint32_t)rank;
+      kout[pos] = k;
+      vout[pos] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Stable sort of (keys, vals) by the low `bits` key bits. Returns true when the
+// result ended in the *_alt buffers.
+bool radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int n, int bits,
+                      uint32_t* counts, cudaStream_t s, int64_t* launches) {
+  if (n <= 0) return false;
+  const int nb = radix_blocks(n);
+  uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
+  bool alt = false;
+  for (int shift = 0; shift < bits; shift += 8) {
+    const int w = min(8, bits - shift);
+    const uint32_t mask = (1u << w) - 1u;
+    radix_hist<<<nb, SORT_THREADS, 0, s>>>(ki, n, shift, mask, counts, nb);
+    scan_exclusive<<<1, 1024, 0, s>>>(counts, 256 * nb);
+    radix_scatter<<<nb, SORT_THREADS, 0, s>>>(ki, vi, ko, vo, counts, n, shift, mask, nb);
+    *launches += 3;
+    uint32_t* t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+    alt = !alt;
+  }
+  return alt;
+}
+
+// ---------------------------------------------------------------- CSR runs
+// start[c] = first sorted position whose key is >= c, c = 0..ncells.
+__global__ void csr_kernel(const uint32_t* __restrict__ sk, int n, int ncells, uint32_t* __restrict__ start) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  int prev = (i == 0) ? -1 : (int)sk[i - 1];
+  int cur = (i == n) ? ncells : (int)sk[i];
+  for (int c = prev + 1; c <= cur; ++c) start[c] = (uint32_t)i;
+}
+
+// --------------------------------------------------------------- staging
+__global__ void stage_points_kernel(const double* __restrict__ xyz, const uint32_t* __restrict__ perm, int n,
+                                    double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz,
+                                    float4* __restrict__ pf, const double* __restrict__ wts,
+                                    double* __restrict__ sw, float* __restrict__ swf) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  size_t o = perm[i];
+  double x = xyz[3 * o], y = xyz[3 * o + 1], z = xyz[3 * o + 2];
+  px[i] = x;
+  py[i] = y;
+  pz[i] = z;
+  pf[i] = make_float4((float)x, (float)y, (float)z, 0.f);
+  if (wts) {
+    double w = wts[o];
+    sw[i] = w;
+    swf[i] = (float)w;
+  }
+}
+
+__global__ void stage_soa_kernel(const double* __restrict__ ax, const double* __restrict__ ay,
+                                 const double* __restrict__ az, const uint32_t* __restrict__ perm, int n,
+                                 double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz,
+                                 float4* __restrict__ pf) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t o = perm[i];
+  double x = ax[o], y = ay[o], z = az[o];
+  px[i] = x;
+  py[i] = y;
+  pz[i] = z;
+  pf[i] = make_float4((float)x, (float)y, (float)z, 0.f);
+}
+
+// per fit: values into sorted order (FP64 and the FP32 slot of pf)
+__global__ void stage_values_kernel(const double* __restrict__ y, const uint32_t* __restrict__ perm, int n,
+                                    double* __restrict__ sy, float4* __restrict__ pf, int write64, DevStatus* st) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = y[perm[i]];
+  if (!isfinite(v)) {
+    set_flag(st, ST_NONFINITE);
+    v = 0.0;
+  }
+  if (write64) sy[i] = v;
+  pf[i].w = (float)v;
+}
+
+void build_cells(const CellBuild& cb, cudaStream_t s, int64_t* launches) {
+  const int n = cb.n;
+  const int T = 256;
+  const int gb = (n + T - 1) / T;
+  if (cb.xyz_aos)
+    keys_kernel<<<gb, T, 0, s>>>(cb.xyz_aos, n, cb.B, cb.P, cb.keys, cb.vals, cb.st);
+  else
+    keys_kernel_soa<<<gb, T, 0, s>>>(cb.ax, cb.ay, cb.az, n, cb.B, cb.P, cb.keys, cb.vals);
+  ++*launches;
+  int bits = 0;
+  while ((1u << bits) < (uint32_t)(cb.B * cb.P)) ++bits;
+  bool alt = radix_sort_pairs(cb.keys, cb.vals, cb.keys_alt, cb.vals_alt, n, bits, cb.counts, s, launches);
+  const uint32_t* sk = alt ? cb.keys_alt : cb.keys;
+  const uint32_t* perm = alt ? cb.vals_alt : cb.vals;
+  csr_kernel<<<(n + 1 + T - 1) / T, T, 0, s>>>(sk, n, cb.B * cb.P, cb.start);
+  ++*launches;
+  if (cb.xyz_aos)
+    stage_points_kernel<<<gb, T, 0, s>>>(cb.xyz_aos, perm, n, cb.px, cb.py, cb.pz, cb.pf, cb.wts, cb.sw, cb.swf);
+  else
+    stage_soa_kernel<<<gb, T, 0, s>>>(cb.ax, cb.ay, cb.az, perm, n, cb.px, cb.py, cb.pz, cb.pf);
+  ++*launches;
+  *cb.perm_out = perm;
+  *cb.keys_out = sk;
+}
+
+void stage_values(const double* y, const uint32_t* perm, int n, double* sy, float4* pf, bool write64,
+                  DevStatus* st, cudaStream_t s, int64_t* launches) {
+  const int T = 256;
+  stage_values_kernel<<<(n + T - 1) / T, T, 0, s>>>(y, perm, n, sy, pf, write64 ? 1 : 0, st);
+  ++*launches;
+}
+
+}  // namespace hamls

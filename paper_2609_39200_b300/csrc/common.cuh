@@ -1,0 +1,308 @@
+// common.cuh - shared device helpers of the HAMLS library (sm_103a).
+//
+// Neighbour structure. Points on S^2 are bucketed into B latitude bands and P
+// longitude cells per band. The band coordinate is
+//   zeta(z) = sign(z) (1 - sqrt(1 - |z|)),
+// which is close to linear in the colatitude (bands are 2.8/B to 4/B rad
+// wide), and the longitude coordinate is the "diamond" parameter
+//   psi = quadrant + |.| / (|x| + |y|)  in [0, 4),
+// a monotone function of the longitude that needs one IEEE division and no
+// transcendental function. Keys key = band * P + cell are therefore computed
+// bit-identically by any IEEE-754 implementation that uses the same formula.
+// Sorting the points by key makes every (band, cell range) a contiguous run
+// of the sorted arrays, so a spherical cap is enumerated as at most two
+// contiguous runs per band, found through a CSR array start[B*P + 1].
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+namespace hamls {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int KMAX = 4;          // MLS degree limit (m <= 15)
+constexpr int KNN_MAX = 128;     // largest n for the k-nearest-neighbour search
+
+// device status bits (reported by hamls_sync)
+enum : unsigned {
+  ST_UNDERDET = 1u,     // fewer than m nodes in a support after the guard
+  ST_SUPPORT = 2u,      // delta >= pi/2
+  ST_NONFINITE = 4u,    // non-finite value
+  ST_BADNODE = 8u,      // node not a unit vector / not finite
+  ST_KNN = 16u,         // k-nearest-neighbour search did not converge (M < n)
+};
+
+// device counters
+enum { C_SUM_N = 0, C_MIN_N, C_MAX_N, C_REG, C_GUARD, C_REDO, C_DROP, C_GUARD_LIST, C_REDO_LIST,
+       C_BATCH, C_NCOUNT };
+
+struct DevStatus {
+  unsigned flags;
+  unsigned pad;
+  unsigned long long cnt[16];
+};
+
+// A point set with its band/cell structure (sorted order).
+struct Cells {
+  int B, P;                 // bands, cells per band (P multiple of 4)
+  int n;                    // number of points
+  const uint32_t* start;    // CSR over cells, B*P + 1 entries
+  const float4* pf;         // sorted points, FP32 (x, y, z, value slot)
+  const double* px;         // sorted points, FP64 SoA
+  const double* py;
+  const double* pz;
+  const uint32_t* perm;     // sorted position -> original index
+};
+
+// ---------------------------------------------------------------- warp utils
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void set_flag(DevStatus* st, unsigned f) { atomicOr(&st->flags, f); }
+
+// ------------------------------------------------------------ exact cell key
+// Bit-exact: only IEEE add/sub/mul/div/sqrt with round-to-nearest, no FMA.
+__device__ __forceinline__ uint32_t cell_key64(double x, double y, double z, int B, int P) {
+  double az = fabs(z);
+  double s = __dsqrt_rn(__dsub_rn(1.0, az));
+  double om = __dsub_rn(1.0, s);
+  double zeta = (z < 0) ? -om : om;
+  int band = (int)floor(__dmul_rn(__dadd_rn(zeta, 1.0), (double)(B / 2)));
+  band = min(max(band, 0), B - 1);
+  double ax = fabs(x), ay = fabs(y);
+  double den = __dadd_rn(ax, ay);
+  int q;
+  double num;
+  if (x > 0 && y >= 0) { q = 0; num = ay; }
+  else if (x <= 0 && y > 0) { q = 1; num = ax; }
+  else if (x < 0 && y <= 0) { q = 2; num = ay; }
+  else if (x >= 0 && y < 0) { q = 3; num = ax; }
+  else { q = 0; num = 0.0; }
+  double frac = den > 0 ? __ddiv_rn(num, den) : 0.0;
+  int qc = P / 4;
+  int w = (int)floor(__dmul_rn(frac, (double)qc));
+  w = min(max(w, 0), qc - 1);
+  return (uint32_t)(band * P + q * qc + w);
+}
+
+// FP32 versions used only to enumerate candidates (with margins).
+__device__ __forceinline__ int band_of_f(float z, int B) {
+  float s = sqrtf(fmaxf(0.f, 1.f - fabsf(z)));
+  float zeta = (z < 0.f) ? -(1.f - s) : (1.f - s);
+  int b = (int)floorf((zeta + 1.f) * (0.5f * (float)B));
+  return min(max(b, 0), B - 1);
+}
+
+__device__ __forceinline__ int cell_of_f(float x, float y, int P) {
+  float ax = fabsf(x), ay = fabsf(y), den = ax + ay;
+  int q;
+  float num;
+  if (x > 0.f && y >= 0.f) { q = 0; num = ay; }
+  else if (x <= 0.f && y > 0.f) { q = 1; num = ax; }
+  else if (x < 0.f && y <= 0.f) { q = 2; num = ay; }
+  else if (x >= 0.f && y < 0.f) { q = 3; num = ax; }
+  else { q = 0; num = 0.f; }
+  float frac = den > 0.f ? num / den : 0.f;
+  int qc = P / 4;
+  int w = min(max((int)floorf(frac * (float)qc), 0), qc - 1);
+  return q * qc + w;
+}
+
+__device__ __forceinline__ float zeta_to_z(float zeta) {
+  return zeta >= 0.f ? 1.f - (1.f - zeta) * (1.f - zeta) : (1.f + zeta) * (1.f + zeta) - 1.f;
+}
+
+// ------------------------------------------------------------- cap queries
+// Geodesic cap of radius r around a unit vector q, prepared for candidate
+// enumeration in FP32. Every margin enlarges the enumerated set; the caller
+// decides membership with its own exact test.
+struct Cap {
+  float zq, sq, cph, sph;   // cos/sin colatitude, cos/sin longitude of q
+  float cr;                 // cos r
+  float zlo, zhi;           // z extent of the cap, widened
+  float cstar;              // cos of the largest longitude half-width
+  int polar;                // enumerate whole bands (q at a pole, or r >= pi/2)
+};
+
+__device__ __forceinline__ Cap make_cap(double qx, double qy, double qz, double r) {
+  Cap c;
+  float fr = fminf((float)r * (1.f + 2e-5f) + 2e-6f, 3.14159265f);
+  float cr, sr;
+  sincosf(fr, &sr, &cr);
+  double sq64 = sqrt(qx * qx + qy * qy);
+  c.zq = (float)qz;
+  c.sq = (float)sq64;
+  c.cr = cr;
+  if (sq64 > 1e-12) {
+    c.cph = (float)(qx / sq64);
+    c.sph = (float)(qy / sq64);
+  } else {
+    c.cph = 1.f;
+    c.sph = 0.f;
+  }
+  c.polar = (c.sq < 1e-6f) || (cr <= 1e-4f);
+  float zhi = (c.zq >= cr) ? 1.f : c.zq * cr + c.sq * sr;
+  float zlo = (-c.zq >= cr) ? -1.f : c.zq * cr - c.sq * sr;
+  c.zhi = fminf(1.f, zhi + 4e-6f);
+  c.zlo = fmaxf(-1.f, zlo - 4e-6f);
+  float ratio = sr / fmaxf(c.sq, 1e-30f);
+  c.cstar = (ratio >= 1.f) ? -1.f : sqrtf(1.f - ratio * ratio);
+  return c;
+}
+
+// cos of the longitude half-width of the cap at height z
+__device__ __forceinline__ float cap_cos_halfwidth(const Cap& c, float z) {
+  float den = sqrtf(fmaxf(0.f, 1.f - z * z)) * c.sq;
+  return den > 1e-20f ? (c.cr - z * c.zq) / den : -1.f;
+}
+
+// The (at most two) contiguous runs of sorted points of band b that can lie
+// in the cap: [s0, s0+n0) and [s1, s1+n1).
+__device__ __forceinline__ void band_runs(const Cells& g, const Cap& c, int b, uint32_t& s0,
+                                          uint32_t& n0, uint32_t& s1, uint32_t& n1) {
+  n0 = n1 = 0;
+  s0 = s1 = 0;
+  const int B = g.B, P = g.P;
+  float za = zeta_to_z(-1.f + 2.f * (float)b / (float)B);
+  float zb = zeta_to_z(-1.f + 2.f * (float)(b + 1) / (float)B);
+  if (fmaxf(za, c.zlo) > fminf(zb, c.zhi)) return;       // band outside the cap's z extent
+  // the band's z interval, widened past the FP32 rounding of its edges
+  float lo = fmaxf(za - 1e-6f, c.zlo), hi = fminf(zb + 1e-6f, c.zhi);
+  const uint32_t base = (uint32_t)b * (uint32_t)P;
+  // near a pole the half-width is ill-conditioned in FP32: take the whole band
+  float smin = fminf(sqrtf(fmaxf(0.f, 1.f - lo * lo)), sqrtf(fmaxf(0.f, 1.f - hi * hi)));
+  bool full = c.polar || (smin * c.sq < 1e-2f);
+  float cmin = -1.f;
+  if (!full) {
+    cmin = fminf(cap_cos_halfwidth(c, lo), cap_cos_halfwidth(c, hi));
+    float zs = c.zq / c.cr;
+    if (zs > lo && zs < hi) cmin = fminf(cmin, c.cstar);
+    cmin -= 2e-5f;
+    full = !(cmin > 0.f);
+  }
+  if (!full) {
+    cmin = fminf(cmin, 1.f);
+    float sd = sqrtf(fmaxf(0.f, 1.f - cmin * cmin));
+    float xa = c.cph * cmin + c.sph * sd, ya = c.sph * cmin - c.cph * sd;   // phi_q - dphi
+    float xb = c.cph * cmin - c.sph * sd, yb = c.sph * cmin + c.cph * sd;   // phi_q + dphi
+    int ca = cell_of_f(xa, ya, P), cb = cell_of_f(xb, yb, P);
+    int lo_c = ca - 1, hi_c = cb + 1;
+    if (ca > cb) hi_c += P;
+    if (hi_c - lo_c + 1 >= P) {
+      full = true;
+    } else if (lo_c < 0) {
+      s0 = g.start[base + lo_c + P];
+      n0 = g.start[base + P] - s0;
+      s1 = g.start[base];
+      n1 = g.start[base + hi_c + 1] - s1;
+    } else if (hi_c >= P) {
+      s0 = g.start[base + lo_c];
+      n0 = g.start[base + P] - s0;
+      s1 = g.start[base];
+      n1 = g.start[base + hi_c - P + 1] - s1;
+    } else {
+      s0 = g.start[base + lo_c];
+      n0 = g.start[base + hi_c + 1] - s0;
+    }
+  }
+  if (full) {
+    s0 = g.start[base];
+    n0 = g.start[base + P] - s0;
+    n1 = 0;
+  }
+}
+
+__device__ __forceinline__ void cap_band_range(const Cells& g, const Cap& c, int& b_lo, int& b_hi) {
+  b_lo = max(band_of_f(c.zlo, g.B) - 1, 0);
+  b_hi = min(band_of_f(c.zhi, g.B) + 1, g.B - 1);
+}
+
+// Warp-cooperative enumeration of every sorted point index that can lie in
+// the cap. The runs of 32 consecutive bands are concatenated and dealt to the
+// lanes 32 at a time, so consecutive lanes read consecutive points. f(valid,
+// idx) is called by all 32 lanes together (it may use warp intrinsics).
+template <class F>
+__device__ __forceinline__ void for_cap_candidates(const Cells& g, const Cap& c, F&& f) {
+  const int lane = threadIdx.x & 31;
+  int b_lo, b_hi;
+  cap_band_range(g, c, b_lo, b_hi);
+  for (int b0 = b_lo; b0 <= b_hi; b0 += 32) {
+    const int b = b0 + lane;
+    uint32_t s0 = 0, n0 = 0, s1 = 0, n1 = 0;
+    if (b <= b_hi) band_runs(g, c, b, s0, n0, s1, n1);
+    const uint32_t len = n0 + n1;
+    uint32_t incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const uint32_t excl = incl - len;
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    for (uint32_t base = 0; base < total; base += 32) {
+      const uint32_t v = base + lane;
+      int owner = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        int cand = owner + step;
+        uint32_t e = __shfl_sync(FULL, excl, cand & 31);
+        if (cand < 32 && e <= v) owner = cand;
+      }
+      const uint32_t oe = __shfl_sync(FULL, excl, owner);
+      const uint32_t os0 = __shfl_sync(FULL, s0, owner);
+      const uint32_t on0 = __shfl_sync(FULL, n0, owner);
+      const uint32_t os1 = __shfl_sync(FULL, s1, owner);
+      const bool valid = v < total;
+      const uint32_t off = v - oe;
+      const uint32_t idx = valid ? ((off < on0) ? os0 + off : os1 + (off - on0)) : 0u;
+      f(valid, idx);
+    }
+  }
+}
+
+// Number of candidates the enumeration would visit (no point is read).
+__device__ __forceinline__ uint32_t cap_box_count(const Cells& g, const Cap& c) {
+  const int lane = threadIdx.x & 31;
+  int b_lo, b_hi;
+  cap_band_range(g, c, b_lo, b_hi);
+  uint32_t tot = 0;
+  for (int b0 = b_lo; b0 <= b_hi; b0 += 32) {
+    const int b = b0 + lane;
+    uint32_t s0 = 0, n0 = 0, s1 = 0, n1 = 0;
+    if (b <= b_hi) band_runs(g, c, b, s0, n0, s1, n1);
+    tot += n0 + n1;
+  }
+  return warp_sum(tot);
+}
+
+// ----------------------------------------------------------- exact distance
+// |x - q|^2 in FP64 with a fixed order and no contraction.
+__device__ __forceinline__ double chord2_exact(double x, double y, double z, double qx, double qy, double qz) {
+  double dx = __dsub_rn(x, qx), dy = __dsub_rn(y, qy), dz = __dsub_rn(z, qz);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Wendland phi_{3,2}(r) = (1-r)^6 (35 r^2 + 18 r + 3) on [0,1).
+template <typename T>
+__device__ __forceinline__ T wendland(T r) {
+  T om = r < T(1) ? T(1) - r : T(0);
+  T om2 = om * om;
+  T om6 = om2 * om2 * om2;
+  return om6 * ((T(35) * r + T(18)) * r + T(3));
+}
+
+__device__ __forceinline__ double geodesic_from_chord2(double c2) { return 2.0 * asin(0.5 * sqrt(c2)); }
+__device__ __forceinline__ float geodesic_from_chord2(float c2) { return 2.f * asinf(0.5f * sqrtf(c2)); }
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+}  // namespace hamls

@@ -1,0 +1,147 @@
+// grid.cu - Algorithm 1 step 1 and the plan-time tables of step 3.
+//
+// The S^2 product rule of Sec. 2.1: Gauss-Legendre nodes t_k in cos(theta)
+// (N+1 nodes, descending), phi_j = 2 pi j / (2N+2). Gauss-Legendre nodes come
+// from Newton's method on P_{N+1} (three-term recurrence), weights from
+// w = 2 / ((1 - t^2) P'_{N+1}(t)^2).
+//
+// Step 3 on this grid is fhat_l^m = (2 pi/(2N+2)) sum_k w_k Pbar_l^m(t_k) F_k(m)
+// (eq. quadrature_based_approximation with the product weights). The matrix
+// A^m[l, k] = (2 pi/(2N+2)) w_k Pbar_l^m(t_k) is generated once per plan by
+// the normalised three-term recurrence in FP64 and folded over the equator:
+// t_{N-k} = -t_k and Pbar_l^m(-t) = (-1)^{l+m} Pbar_l^m(t), so only the
+// hc = floor(N/2) + 1 northern columns are stored.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace hamls {
+
+__global__ void gl_kernel(int N, double* t_out, double* w_out, double* s_out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > N) return;
+  const int n = N + 1;
+  double t = cospi((k + 0.75) / (n + 0.5));
+  double p0 = 1.0, p1 = t;
+  for (int it = 0; it < 100; ++it) {
+    p0 = 1.0;
+    p1 = t;
+    for (int j = 2; j <= n; ++j) {
+      double p2 = ((2 * j - 1) * t * p1 - (j - 1) * p0) / j;
+      p0 = p1;
+      p1 = p2;
+    }
+    if (n == 1) p0 = 1.0;
+    double dp = n * (t * p1 - p0) / (t * t - 1.0);
+    double dt = p1 / dp;
+    t -= dt;
+    if (fabs(dt) < 1e-17) break;
+  }
+  p0 = 1.0;
+  p1 = t;
+  for (int j = 2; j <= n; ++j) {
+    double p2 = ((2 * j - 1) * t * p1 - (j - 1) * p0) / j;
+    p0 = p1;
+    p1 = p2;
+  }
+  if (n == 1) p0 = 1.0;
+  double dp = n * (t * p1 - p0) / (t * t - 1.0);
+  t_out[k] = t;
+  w_out[k] = 2.0 / ((1.0 - t * t) * dp * dp);
+  s_out[k] = sqrt((1.0 - t) * (1.0 + t));
+}
+
+__global__ void phi_kernel(int L, double* cphi, double* sphi, double2* W64, float2* W32) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= L) return;
+  double s, c;
+  sincospi(2.0 * j / L, &s, &c);     // angle 2 pi j / L, argument exact
+  cphi[j] = c;
+  sphi[j] = s;
+  W64[j] = make_double2(c, -s);      // exp(-2 pi i j / L)
+  if (W32) W32[j] = make_float2((float)c, (float)-s);
+}
+
+// a_lm = sqrt((4l^2 - 1)/(l^2 - m^2)), b_lm = sqrt(((l-1)^2 - m^2)/(4(l-1)^2 - 1)),
+// packed m-major like the coefficients.
+__global__ void rec_kernel(int N, double* a_rec, double* b_rec) {
+  int m = blockIdx.x;
+  for (int l = m + threadIdx.x; l <= N; l += blockDim.x) {
+    size_t o = (size_t)m * (N + 1) - (size_t)m * (m - 1) / 2 + (l - m);
+    double a = 0.0, b = 0.0;
+    if (l >= m + 2) {
+      double ll = l, mm = m;
+      a = sqrt((4.0 * ll * ll - 1.0) / (ll * ll - mm * mm));
+      b = sqrt(((ll - 1.0) * (ll - 1.0) - mm * mm) / (4.0 * (ll - 1.0) * (ll - 1.0) - 1.0));
+    }
+    a_rec[o] = a;
+    b_rec[o] = b;
+  }
+}
+
+// one thread per (m, folded column c): Pbar_l^m(t_c) for l = m..N
+__global__ void legendre_gen_kernel(int N, int hc, const double* __restrict__ t, const double* __restrict__ w,
+                                    const double* __restrict__ s, const double* __restrict__ a_rec,
+                                    const double* __restrict__ b_rec, double* __restrict__ A64,
+                                    float* __restrict__ A32) {
+  const int m = blockIdx.y;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= hc) return;
+  const double tc = t[c], sc = s[c];
+  const double h = 2.0 * 3.14159265358979323846 / (2.0 * N + 2.0) * w[c];
+  double pmm = 0.28209479177387814347;   // 1/sqrt(4 pi)
+  for (int k = 1; k <= m; ++k) pmm *= -sqrt((2.0 * k + 1.0) / (2.0 * k)) * sc;
+  const size_t row0 = (size_t)m * (N + 1) - (size_t)m * (m - 1) / 2;
+  double pm2 = 0.0, pm1 = 0.0;          // Pbar_{l-2}^m, Pbar_{l-1}^m
+  for (int l = m; l <= N; ++l) {
+    double p;
+    if (l == m) {
+      p = pmm;
+    } else if (l == m + 1) {
+      p = sqrt(2.0 * m + 3.0) * tc * pmm;
+    } else {
+      const size_t o = row0 + (l - m);
+      p = a_rec[o] * (tc * pm1 - b_rec[o] * pm2);
+    }
+    pm2 = pm1;
+    pm1 = p;
+    const size_t idx = (row0 + (l - m)) * hc + c;
+    const double v = h * p;
+    if (A64) A64[idx] = v;
+    if (A32) A32[idx] = (float)v;
+  }
+}
+
+void build_grid_tables(GridTables& g, bool want32, bool want64, cudaStream_t s, int64_t* launches) {
+  const int N = g.N, L = 2 * N + 2;
+  gl_kernel<<<(N + 1 + 127) / 128, 128, 0, s>>>(N, g.t, g.w, g.s);
+  phi_kernel<<<(L + 255) / 256, 256, 0, s>>>(L, g.cphi, g.sphi, g.W64, want32 ? g.W32 : nullptr);
+  rec_kernel<<<N + 1, 256, 0, s>>>(N, g.a_rec, g.b_rec);
+  dim3 grid((g.hc + 63) / 64, N + 1);
+  legendre_gen_kernel<<<grid, 64, 0, s>>>(N, g.hc, g.t, g.w, g.s, g.a_rec, g.b_rec, want64 ? g.A64 : nullptr,
+                                          want32 ? g.A32 : nullptr);
+  *launches += 4;
+}
+
+// Fibonacci grid: z_i = 1 - (2i+1)/n, phi_i = 2 pi {i (1 - 1/Phi)} with the
+// fractional part taken exactly in 0.64 fixed point and truncated to 53 bits.
+__global__ void fibonacci_kernel(double* x, double* y, double* z, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned long long G = 0x61C8864680B583EAull;
+  unsigned long long f = ((unsigned long long)i * G) >> 11;
+  double frac = (double)f * 0x1p-53;
+  double zz = 1.0 - (2.0 * i + 1.0) / (double)n;
+  double sn, cs;
+  sincospi(2.0 * frac, &sn, &cs);
+  double r = sqrt((1.0 - zz) * (1.0 + zz));
+  x[i] = r * cs;
+  y[i] = r * sn;
+  z[i] = zz;
+}
+
+void fibonacci_points(double* x, double* y, double* z, int n, cudaStream_t s, int64_t* launches) {
+  fibonacci_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, y, z, n);
+  ++*launches;
+}
+
+}  // namespace hamls

@@ -1,0 +1,107 @@
+// kernels.h - host-side launchers shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "common.cuh"
+
+namespace hamls {
+
+// ------------------------------------------------------------------ cells.cu
+struct CellBuild {
+  int n, B, P;
+  const double* xyz_aos;            // n x 3 input (or NULL, then ax/ay/az)
+  const double *ax, *ay, *az;
+  const double* wts;                // optional per-point weights (AoS input only)
+  uint32_t *keys, *vals, *keys_alt, *vals_alt, *counts;
+  uint32_t* start;                  // B*P + 1
+  double *px, *py, *pz, *sw;
+  float4* pf;
+  float* swf;
+  DevStatus* st;
+  const uint32_t** perm_out;        // receives the sorted -> original permutation
+  const uint32_t** keys_out;        // receives the sorted keys
+};
+int radix_blocks(int n);
+void build_cells(const CellBuild& cb, cudaStream_t s, int64_t* launches);
+bool radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int n, int bits,
+                      uint32_t* counts, cudaStream_t s, int64_t* launches);
+void stage_values(const double* y, const uint32_t* perm, int n, double* sy, float4* pf, bool write64,
+                  DevStatus* st, cudaStream_t s, int64_t* launches);
+
+// ------------------------------------------------------------------- grid.cu
+struct GridTables {
+  int N;
+  double *t, *w, *s;            // N+1: cos theta_k (descending), GL weight, sin theta_k
+  double *cphi, *sphi;          // 2N+2
+  double *a_rec, *b_rec;        // packed (N+1)(N+2)/2 recurrence coefficients
+  double* A64;                  // folded Legendre quadrature matrix, ncoef x hc
+  float* A32;
+  double2* W64;                 // FFT twiddles exp(-2 pi i j / L), L = 2N+2
+  float2* W32;
+  int hc;                       // folded column count
+};
+void build_grid_tables(GridTables& g, bool want32, bool want64, cudaStream_t s, int64_t* launches);
+void fibonacci_points(double* x, double* y, double* z, int n, cudaStream_t s, int64_t* launches);
+
+// -------------------------------------------------------------------- knn.cu
+struct SupportArgs {
+  Cells nodes;                  // scattered nodes
+  Cells aux;                    // auxiliary grid
+  int n_target, m, N;
+  double eps, rho_aux;
+  const double *ring_t, *ring_s, *cphi, *sphi;
+  double* dn_aux_sorted;        // aux d_n (geodesic), sorted aux order
+  double* delta;                // M_Q
+  double* rho2;                 // M_Q
+  int32_t* count;               // M_Q
+  uint8_t* guarded;             // M_Q
+  uint32_t* guard_list;         // M_Q
+  uint32_t* order_keys;         // M_Q (cost keys)
+  uint32_t* order_vals;         // M_Q
+  int fp64;                     // 1: FP64 Shepard, 0: FP32
+  DevStatus* st;
+};
+void run_aux_knn(const SupportArgs& a, cudaStream_t s, int64_t* launches);
+void run_shepard(const SupportArgs& a, cudaStream_t s, int64_t* launches);
+void run_counts(const SupportArgs& a, cudaStream_t s, int64_t* launches);
+void run_knn_queries(const Cells& nodes, const double* q, int64_t nq, int n, double* c2_out, DevStatus* st,
+                     cudaStream_t s, int64_t* launches);
+void run_ball_queries(const Cells& nodes, const double* q, const double* rho2, int64_t nq, int64_t* count,
+                      int64_t* idsum, uint64_t* idhash, cudaStream_t s, int64_t* launches);
+
+// -------------------------------------------------------------------- mls.cu
+struct MlsArgs {
+  Cells nodes;
+  const double* sy;             // sorted values (FP64 form)
+  const double* sw;             // sorted node weights or NULL
+  const float* swf;
+  const double *ring_t, *ring_s, *cphi, *sphi;
+  int N, K;
+  const double* delta;
+  const double* rho2;
+  const uint32_t* order;        // grid nodes, heaviest first
+  int MQ;
+  double* fgrid;
+  double* chi;
+  double* tau;
+  double chiT, chiF, floor_, fp64_pivot;
+  double mu[KMAX + 1];
+  float* redo_mom;              // MIXED: moments of nodes re-solved in FP64
+  uint32_t* redo_node;
+  DevStatus* st;
+  int num_sms;
+};
+void run_mls(const MlsArgs& a, bool mixed, cudaStream_t s, int64_t* launches);
+
+// ------------------------------------------------------------------- quad.cu
+struct QuadArgs {
+  const GridTables* g;
+  const double* fgrid;          // M_Q ring-major
+  void* F;                      // (N+1) x (N+1) complex, T
+  double* coeffs;               // (N+1)(N+2)/2 complex
+  int radices[32];
+  int nrad;
+};
+void run_quadrature(const QuadArgs& a, bool mixed, cudaStream_t s, int64_t* launches);
+
+}  // namespace hamls

@@ -1,0 +1,390 @@
+// mls.cu - Algorithm 1 step 2: the regularised MLS value at every quadrature
+// node (Sec. 2.2, 2.3).
+//
+// Per grid node q with support radius delta and local nodes X(q) (open
+// geodesic ball, eq. mls_local_node_set):
+//   weights   w_i = v_i phi(d(q, x_i)/delta), Wendland phi (eq. weight_function_radial);
+//   basis     monomials u^a v^b, a + b <= K, of the tangent coordinates of the
+//             orthogonal projection onto T_q S^2 (Pi_K^tan), ascending degree;
+//   Gram      H = B^T B of eq. (mls local vectors) with unit-norm columns. It is
+//             assembled from the weighted moments sum_i w_i u^a v^b (a+b <= 2K)
+//             and sum_i w_i y_i u^a v^b (a+b <= K): every Gram entry is one
+//             moment, scaled by the column norms and the weight sum;
+//   solve     C = L L^T (eq. mls local Cholesky factor), d = L^{-1} b,
+//             e = L^{-1} z, r_0 = |d|^2, chi = 1/(1 - r_0) (eq. chi via
+//             coupling); if chi > chi_T, tau by bisection on
+//             r_tau = sum_j d_j^2 / (1 + tau mu_j) = 1 - 1/chi_T (eq.
+//             regularized MLS amplification); tau~ = S(t) tau with the C^3
+//             smoothstep S and t = (chi - chi_T)/(chi_full - chi_T);
+//   value     c_1 = (beta - sum_j d_j e_j/(1 + tau~ mu_j)) / (1 - sum_j d_j^2/(1 + tau~ mu_j)),
+//             the first coefficient of the regularised problem (eq. regularized
+//             MLS problem) in closed form (Schur complement of its normal equations).
+//
+// Execution: a warp takes 32 grid nodes (heaviest first). For each node the 32
+// lanes stream its candidates (coalesced runs of the sorted points), test the
+// ball, accumulate the moments and reduce them with shuffles; the reduced
+// moments are parked in shared memory. Then the 32 lanes solve the 32 local
+// problems side by side, one per lane.
+//
+// Precision forms: FP64 (everything in double) and MIXED (FP32 gather and
+// moments on centred, delta-scaled coordinates, FP32 solve; nodes whose FP32
+// Cholesky meets a tiny pivot are re-solved in FP64 by a second kernel).
+#include <type_traits>
+#include "common.cuh"
+#include "kernels.h"
+
+namespace hamls {
+
+__host__ __device__ constexpr int dim_tan(int K) { return (K + 1) * (K + 2) / 2; }
+__host__ __device__ constexpr int deg_of(int j) {
+  int k = 0;
+  while ((k + 1) * (k + 2) / 2 <= j) ++k;
+  return k;
+}
+__host__ __device__ constexpr int ea_of(int j) { return deg_of(j) - (j - deg_of(j) * (deg_of(j) + 1) / 2); }
+__host__ __device__ constexpr int eb_of(int j) { return j - deg_of(j) * (deg_of(j) + 1) / 2; }
+__host__ __device__ constexpr int midx(int a, int b, int D) { return b * (D + 1) - b * (b - 1) / 2 + a; }
+__host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+template <int K>
+struct Shape {
+  static constexpr int m = dim_tan(K);
+  static constexpr int mm = m - 1;
+  static constexpr int NM = dim_tan(2 * K);   // weighted moments, degree <= 2K
+  static constexpr int NY = dim_tan(K);       // value moments, degree <= K
+  static constexpr int NV = NM + NY;
+};
+
+struct SolveParams {
+  double chiT, chiF, floor_;
+  double mu[KMAX + 1];
+};
+
+template <typename S>
+__device__ __forceinline__ S smoothstep3(S t) {
+  S t2 = t * t;
+  return t2 * t2 * (S(35) + t * (S(-84) + t * (S(70) - S(20) * t)));
+}
+
+template <typename S>
+__device__ __forceinline__ S rsqrt_t(S x);
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+
+// The local problem from its moments. mw: NM weighted moments, my: NY value
+// moments (unnormalised weights). Returns c1; also chi, tau~, the smallest
+// squared pivot and the number of dropped directions.
+template <typename S, int K>
+__device__ __forceinline__ S solve_local(const S* mw, const S* my, const SolveParams& P, S& chi_out, S& tau_out,
+                                         S& minpiv, int& ndrop) {
+  constexpr int m = Shape<K>::m, mm = m - 1, D2 = 2 * K, D1 = K;
+  const S W = mw[0];
+  S is[m];
+#pragma unroll
+  for (int j = 1; j < m; ++j) {
+    const S g = mw[midx(2 * ea_of(j), 2 * eb_of(j), D2)];
+    is[j] = g > S(0) ? rsqrt_t<S>(g) : S(0);
+  }
+  const S isW = rsqrt_t<S>(W);
+  S L[mm * (mm + 1) / 2];
+#pragma unroll
+  for (int i = 0; i < mm; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j)
+      L[tri(i, j)] = mw[midx(ea_of(i + 1) + ea_of(j + 1), eb_of(i + 1) + eb_of(j + 1), D2)] * is[i + 1] * is[j + 1];
+  S bv[mm], zv[mm];
+#pragma unroll
+  for (int j = 0; j < mm; ++j) {
+    bv[j] = mw[midx(ea_of(j + 1), eb_of(j + 1), D2)] * is[j + 1] * isW;
+    zv[j] = my[midx(ea_of(j + 1), eb_of(j + 1), D1)] * is[j + 1] * isW;
+  }
+  const S beta = my[0] / W;
+  // Cholesky with the pivot floor
+  bool drop[mm];
+  minpiv = S(1);
+  ndrop = 0;
+#pragma unroll
+  for (int j = 0; j < mm; ++j) {
+    S sjj = L[tri(j, j)];
+#pragma unroll
+    for (int k = 0; k < j; ++k) sjj -= L[tri(j, k)] * L[tri(j, k)];
+    drop[j] = !(sjj > S(P.floor_));
+    ndrop += drop[j] ? 1 : 0;
+    minpiv = sjj < minpiv ? sjj : minpiv;
+    const S ljj = drop[j] ? S(0) : sqrt(sjj);
+    const S inv = drop[j] ? S(0) : S(1) / ljj;
+    L[tri(j, j)] = ljj;
+#pragma unroll
+    for (int i = j + 1; i < mm; ++i) {
+      S v = L[tri(i, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) v -= L[tri(i, k)] * L[tri(j, k)];
+      L[tri(i, j)] = v * inv;
+    }
+  }
+  // d = L^{-1} b, e = L^{-1} z, grouped by degree
+  S d[mm], e[mm];
+  S Dl[K + 1], Sl[K + 1];
+#pragma unroll
+  for (int l = 0; l <= K; ++l) Dl[l] = Sl[l] = S(0);
+#pragma unroll
+  for (int j = 0; j < mm; ++j) {
+    S vb = bv[j], vz = zv[j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) {
+      vb -= L[tri(j, k)] * d[k];
+      vz -= L[tri(j, k)] * e[k];
+    }
+    const S inv = drop[j] ? S(0) : S(1) / L[tri(j, j)];
+    d[j] = vb * inv;
+    e[j] = vz * inv;
+    Dl[deg_of(j + 1)] += d[j] * d[j];
+    Sl[deg_of(j + 1)] += d[j] * e[j];
+  }
+  S r0 = S(0);
+#pragma unroll
+  for (int l = 1; l <= K; ++l) r0 += Dl[l];
+  const S inf = S(1) / S(0);
+  const S chi = r0 < S(1) ? S(1) / (S(1) - r0) : inf;
+  S tt = S(0);
+  const S chiT = S(P.chiT);
+  if (chi > chiT) {
+    const S rstar = S(1) - S(1) / chiT;
+    S lo = S(0), hi = r0 / (S(P.mu[1]) * rstar);
+    const S tol = sizeof(S) == 8 ? S(1e-16) : S(1e-7);
+    for (int it = 0; it < 200; ++it) {
+      const S mid = S(0.5) * (lo + hi);
+      S r = S(0);
+#pragma unroll
+      for (int l = 1; l <= K; ++l) r += Dl[l] / (S(1) + mid * S(P.mu[l]));
+      if (r > rstar) lo = mid;
+      else hi = mid;
+      if (hi - lo <= tol * hi) break;
+    }
+    const S tau = S(0.5) * (lo + hi);
+    S t = (chi == inf) ? S(1) : (chi - chiT) / (S(P.chiF) - chiT);
+    t = t < S(1) ? t : S(1);
+    tt = smoothstep3(t) * tau;
+  }
+  S num = beta, den = S(1);
+#pragma unroll
+  for (int l = 1; l <= K; ++l) {
+    const S f = S(1) / (S(1) + tt * S(P.mu[l]));
+    num -= Sl[l] * f;
+    den -= Dl[l] * f;
+  }
+  chi_out = chi;
+  tau_out = tt;
+  return num / den;
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void accumulate(T (&acc)[Shape<K>::NV], T w, T u, T v, T y) {
+  constexpr int D2 = 2 * K, D1 = K, NM = Shape<K>::NM;
+  T vb = w;
+#pragma unroll
+  for (int b = 0; b <= D2; ++b) {
+    T t = vb;
+#pragma unroll
+    for (int a = 0; a <= D2 - b; ++a) {
+      acc[midx(a, b, D2)] += t;
+      if (a < D2 - b) t *= u;
+    }
+    if (b < D2) vb *= v;
+  }
+  T vy = w * y;
+#pragma unroll
+  for (int b = 0; b <= D1; ++b) {
+    T t = vy;
+#pragma unroll
+    for (int a = 0; a <= D1 - b; ++a) {
+      acc[NM + midx(a, b, D1)] += t;
+      if (a < D1 - b) t *= u;
+    }
+    if (b < D1) vy *= v;
+  }
+}
+
+constexpr int MLS_WARPS = 4;
+
+template <int K, bool MIXED>
+__global__ void __launch_bounds__(MLS_WARPS * 32) mls_kernel(MlsArgs a, SolveParams P, unsigned long long* batch_ctr) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  constexpr int NV = Shape<K>::NV, NM = Shape<K>::NM;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 32 * NV;
+  const int L = 2 * a.N + 2;
+  for (;;) {
+    unsigned long long batch = 0;
+    if (lane == 0) batch = atomicAdd(batch_ctr, 1ull);
+    batch = __shfl_sync(FULL, batch, 0);
+    const long long first = (long long)batch * 32;
+    if (first >= a.MQ) break;
+    const int nb = (int)min(32ll, (long long)a.MQ - first);
+    for (int jb = 0; jb < nb; ++jb) {
+      const int j = (int)a.order[first + jb];
+      const int k = j / L, jj = j - k * L;
+      const double st = a.ring_s[k], ct = a.ring_t[k], cp = a.cphi[jj], sp = a.sphi[jj];
+      const double qx = st * cp, qy = st * sp, qz = ct;
+      const double delta = a.delta[j], rho2 = a.rho2[j];
+      // tangent frame scaled by 1/delta: e1 = d/dtheta, e2 = d/dphi
+      const double id = 1.0 / delta;
+      const T e1x = T(ct * cp * id), e1y = T(ct * sp * id), e1z = T(-st * id);
+      const T e2x = T(-sp * id), e2y = T(cp * id);
+      const T idT = T(id);
+      T acc[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) acc[i] = T(0);
+      Cap cap = make_cap(qx, qy, qz, delta);
+      if (MIXED) {
+        const float qxf = (float)qx, qyf = (float)qy, qzf = (float)qz, r2f = (float)rho2;
+        for_cap_candidates(a.nodes, cap, [&](bool valid, uint32_t idx) {
+          if (!valid) return;
+          const float4 p = a.nodes.pf[idx];
+          const float dx = p.x - qxf, dy = p.y - qyf, dz = p.z - qzf;
+          const float c2 = dx * dx + dy * dy + dz * dz;
+          if (!(c2 < r2f)) return;
+          float w = wendland(geodesic_from_chord2(c2) * (float)idT);
+          if (a.swf) w *= a.swf[idx];
+          const float u = e1x * dx + e1y * dy + e1z * dz;
+          const float v = e2x * dx + e2y * dy;
+          accumulate<T, K>(acc, (T)w, (T)u, (T)v, (T)p.w);
+        });
+      } else {
+        const float qxf = (float)qx, qyf = (float)qy, qzf = (float)qz;
+        const float hi_f = (float)(rho2 + 1e-6 * sqrt(rho2) + 1e-6 * rho2 + 1e-13);
+        for_cap_candidates(a.nodes, cap, [&](bool valid, uint32_t idx) {
+          if (!valid) return;
+          const float4 p = a.nodes.pf[idx];
+          const float fx = p.x - qxf, fy = p.y - qyf, fz = p.z - qzf;
+          if (fx * fx + fy * fy + fz * fz > hi_f) return;
+          const double X = a.nodes.px[idx], Y = a.nodes.py[idx], Z = a.nodes.pz[idx];
+          const double c2 = chord2_exact(X, Y, Z, qx, qy, qz);
+          if (!(c2 < rho2)) return;
+          const double dx = X - qx, dy = Y - qy, dz = Z - qz;
+          double w = wendland(geodesic_from_chord2(c2) * id);
+          if (a.sw) w *= a.sw[idx];
+          const double u = (double)e1x * dx + (double)e1y * dy + (double)e1z * dz;
+          const double v = (double)e2x * dx + (double)e2y * dy;
+          accumulate<T, K>(acc, (T)w, (T)u, (T)v, (T)a.sy[idx]);
+        });
+      }
+#pragma unroll
+      for (int i = 0; i < NV; ++i) acc[i] = warp_sum(acc[i]);
+      if (lane == jb) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sm[lane * NV + i] = acc[i];
+      }
+    }
+    __syncwarp();
+    // one local problem per lane
+    const bool act = lane < nb;
+    const int j = act ? (int)a.order[first + lane] : 0;
+    T mom[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) mom[i] = act ? sm[lane * NV + i] : (i == 0 ? T(1) : T(0));
+    T chi, tau, minpiv;
+    int ndrop;
+    T c1 = solve_local<T, K>(mom, mom + NM, P, chi, tau, minpiv, ndrop);
+    bool redo = false;
+    if (MIXED) redo = act && (ndrop > 0 || !(minpiv >= T(a.fp64_pivot)) || !isfinite(c1));
+    if (act && !redo) {
+      a.fgrid[j] = (double)c1;
+      a.chi[j] = (double)chi;
+      a.tau[j] = (double)tau;
+    }
+    if (redo) {
+      unsigned long long pos = atomicAdd(&a.st->cnt[C_REDO_LIST], 1ull);
+      a.redo_node[pos] = (uint32_t)j;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) a.redo_mom[pos * NV + i] = (float)mom[i];
+    }
+    unsigned long long nreg = __popc(__ballot_sync(FULL, act && !redo && tau > T(0)));
+    unsigned long long nd = warp_sum((unsigned long long)((act && !redo) ? ndrop : 0));
+    if (lane == 0) {
+      if (nreg) atomicAdd(&a.st->cnt[C_REG], nreg);
+      if (nd) atomicAdd(&a.st->cnt[C_DROP], nd);
+    }
+    __syncwarp();
+  }
+}
+
+// MIXED: FP64 re-solve of the nodes whose FP32 Cholesky met a tiny pivot.
+template <int K>
+__global__ void __launch_bounds__(128) redo_kernel(MlsArgs a, SolveParams P) {
+  constexpr int NV = Shape<K>::NV, NM = Shape<K>::NM;
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)a.st->cnt[C_REDO_LIST];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < total; e0 += stride) {
+    const long long e = e0 + lane;
+    const bool act = e < total;
+    double mom[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) mom[i] = act ? (double)a.redo_mom[e * NV + i] : (i == 0 ? 1.0 : 0.0);
+    double chi, tau, minpiv;
+    int ndrop;
+    double c1 = solve_local<double, K>(mom, mom + NM, P, chi, tau, minpiv, ndrop);
+    if (act) {
+      const int j = (int)a.redo_node[e];
+      a.fgrid[j] = c1;
+      a.chi[j] = chi;
+      a.tau[j] = tau;
+    }
+    unsigned long long nreg = __popc(__ballot_sync(FULL, act && tau > 0.0));
+    unsigned long long nd = warp_sum((unsigned long long)(act ? ndrop : 0));
+    unsigned long long nr = __popc(__ballot_sync(FULL, act));
+    if (lane == 0) {
+      atomicAdd(&a.st->cnt[C_REG], nreg);
+      atomicAdd(&a.st->cnt[C_DROP], nd);
+      atomicAdd(&a.st->cnt[C_REDO], nr);
+    }
+  }
+}
+
+template <int K, bool MIXED>
+static void launch_mls(const MlsArgs& a, const SolveParams& P, unsigned long long* ctr, cudaStream_t s,
+                       int64_t* launches) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  const size_t smem = (size_t)MLS_WARPS * 32 * Shape<K>::NV * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(mls_kernel<K, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mls_kernel<K, MIXED>, MLS_WARPS * 32, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int blocks = per_sm * a.num_sms;
+  mls_kernel<K, MIXED><<<blocks, MLS_WARPS * 32, smem, s>>>(a, P, ctr);
+  ++*launches;
+  if (MIXED) {
+    redo_kernel<K><<<a.num_sms * 4, 128, 0, s>>>(a, P);
+    ++*launches;
+  }
+}
+
+void run_mls(const MlsArgs& a, bool mixed, cudaStream_t s, int64_t* launches) {
+  SolveParams P;
+  P.chiT = a.chiT;
+  P.chiF = a.chiF;
+  P.floor_ = a.floor_;
+  for (int l = 0; l <= KMAX; ++l) P.mu[l] = a.mu[l];
+  unsigned long long* ctr = &a.st->cnt[C_BATCH];
+  switch (a.K * 2 + (mixed ? 1 : 0)) {
+    case 2: launch_mls<1, false>(a, P, ctr, s, launches); break;
+    case 3: launch_mls<1, true>(a, P, ctr, s, launches); break;
+    case 4: launch_mls<2, false>(a, P, ctr, s, launches); break;
+    case 5: launch_mls<2, true>(a, P, ctr, s, launches); break;
+    case 6: launch_mls<3, false>(a, P, ctr, s, launches); break;
+    case 7: launch_mls<3, true>(a, P, ctr, s, launches); break;
+    case 8: launch_mls<4, false>(a, P, ctr, s, launches); break;
+    case 9: launch_mls<4, true>(a, P, ctr, s, launches); break;
+    default: break;
+  }
+}
+
+}  // namespace hamls

@@ -1,0 +1,167 @@
+// quad.cu - Algorithm 1 step 3: fhat = F^H W f on the product grid.
+//
+// Ring DFT. F_k(m) = sum_j f_{kj} e^{-i m phi_j}, m = 0..N, for every ring k.
+// Two real rings are packed into one complex sequence z = f_a + i f_b of
+// length L = 2N+2 and transformed by a self-sorting (Stockham) mixed-radix
+// FFT in shared memory; the spectra separate by conjugate symmetry:
+// F_a(m) = (Z(m) + conj Z(L-m))/2, F_b(m) = (Z(m) - conj Z(L-m))/(2i).
+// L = 2(N+1) has arbitrary prime factors (N = 256 gives 2 * 257), so every
+// radix stage is a generic radix-R pass: output (j, r) of the stage with
+// current sub-transform size Ns is
+//   sum_q in[j + q L/R] * w_L^{q ((j mod Ns) L/(Ns R) + r L/R)},
+// written to position (j / Ns) Ns R + (j mod Ns) + r Ns.
+//
+// Legendre quadrature. fhat_l^m = sum_k A^m[l, k] F_k(m) with the folded
+// matrix of grid.cu: for the northern columns c < hc the pair (c, N - c)
+// contributes A^m[l, c] (F_c + (-1)^{l+m} F_{N-c}). One block per order m
+// stages the even/odd folded vectors in shared memory; one warp per degree l
+// streams its matrix row (coalesced) and reduces with shuffles. A single fit
+// is a matrix-vector product bound by HBM bandwidth on the matrix.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace hamls {
+
+template <typename T>
+struct C2;
+template <>
+struct C2<float> { using t = float2; };
+template <>
+struct C2<double> { using t = double2; };
+
+template <typename T>
+__global__ void __launch_bounds__(256) ring_fft_kernel(const double* __restrict__ f, int N, QuadArgs qa,
+                                                       const typename C2<T>::t* __restrict__ W,
+                                                       typename C2<T>::t* __restrict__ F) {
+  using cT = typename C2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = 2 * N + 2;
+  cT* buf0 = reinterpret_cast<cT*>(smem_raw);
+  cT* buf1 = buf0 + L;
+  const int ra = 2 * blockIdx.x, rb = ra + 1;
+  const bool hasb = rb <= N;
+  for (int j = threadIdx.x; j < L; j += blockDim.x) {
+    T x = (T)f[(size_t)ra * L + j];
+    T y = hasb ? (T)f[(size_t)rb * L + j] : T(0);
+    buf0[j].x = x;
+    buf0[j].y = y;
+  }
+  __syncthreads();
+  cT* in = buf0;
+  cT* out = buf1;
+  int Ns = 1;
+  for (int st = 0; st < qa.nrad; ++st) {
+    const int R = qa.radices[st];
+    const int T_ = L / R;
+    const int NsR = Ns * R;
+    const int strideA = L / NsR, strideB = L / R;
+    for (int o = threadIdx.x; o < L; o += blockDim.x) {
+      const int hi = o / NsR, rem = o - hi * NsR;
+      const int r = rem / Ns, jl = rem - r * Ns;
+      const int j = hi * Ns + jl;
+      int step = jl * strideA + r * strideB;
+      step %= L;
+      int e = 0;
+      T ax = 0, ay = 0;
+      for (int q = 0; q < R; ++q) {
+        const cT v = in[j + q * T_];
+        const cT w = W[e];
+        ax += v.x * w.x - v.y * w.y;
+        ay += v.x * w.y + v.y * w.x;
+        e += step;
+        if (e >= L) e -= L;
+      }
+      out[o].x = ax;
+      out[o].y = ay;
+    }
+    __syncthreads();
+    cT* t = in;
+    in = out;
+    out = t;
+    Ns *= R;
+  }
+  for (int m = threadIdx.x; m <= N; m += blockDim.x) {
+    const cT zm = in[m];
+    const cT zc = in[(L - m) % L];            // Z(L - m), to be conjugated
+    cT fa, fb;
+    fa.x = T(0.5) * (zm.x + zc.x);
+    fa.y = T(0.5) * (zm.y - zc.y);
+    // (Z(m) - conj Z(L-m)) / (2i)
+    const T dx = zm.x - zc.x, dy = zm.y + zc.y;
+    fb.x = T(0.5) * dy;
+    fb.y = T(-0.5) * dx;
+    F[(size_t)ra * (N + 1) + m] = fa;
+    if (hasb) F[(size_t)rb * (N + 1) + m] = fb;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) legendre_kernel(int N, int hc, const T* __restrict__ A,
+                                                       const typename C2<T>::t* __restrict__ F,
+                                                       double* __restrict__ coeffs) {
+  using cT = typename C2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cT* E = reinterpret_cast<cT*>(smem_raw);
+  cT* O = E + hc;
+  const int m = blockIdx.x;
+  for (int c = threadIdx.x; c < hc; c += blockDim.x) {
+    const cT a = F[(size_t)c * (N + 1) + m];
+    const int cs = N - c;
+    if (cs != c) {
+      const cT b = F[(size_t)cs * (N + 1) + m];
+      E[c].x = a.x + b.x;
+      E[c].y = a.y + b.y;
+      O[c].x = a.x - b.x;
+      O[c].y = a.y - b.y;
+    } else {
+      E[c] = a;
+      O[c] = a;
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const size_t row0 = (size_t)m * (N + 1) - (size_t)m * (m - 1) / 2;
+  for (int l = m + warp; l <= N; l += nw) {
+    const cT* G = ((l + m) & 1) ? O : E;
+    const T* row = A + (row0 + (l - m)) * hc;
+    T sr = 0, si = 0;
+    for (int c = lane; c < hc; c += 32) {
+      const T av = row[c];
+      sr += av * G[c].x;
+      si += av * G[c].y;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) {
+      coeffs[2 * (row0 + (l - m))] = (double)sr;
+      coeffs[2 * (row0 + (l - m)) + 1] = (double)si;
+    }
+  }
+}
+
+template <typename T>
+static void launch_quad(const QuadArgs& a, const typename C2<T>::t* W, const T* A, cudaStream_t s,
+                        int64_t* launches) {
+  using cT = typename C2<T>::t;
+  const int N = a.g->N, L = 2 * N + 2, hc = a.g->hc;
+  const size_t smem_fft = 2 * (size_t)L * sizeof(cT);
+  const size_t smem_leg = 2 * (size_t)hc * sizeof(cT);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(ring_fft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(legendre_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  ring_fft_kernel<T><<<(N + 2) / 2, 256, smem_fft, s>>>(a.fgrid, N, a, W, reinterpret_cast<cT*>(a.F));
+  legendre_kernel<T><<<N + 1, 256, smem_leg, s>>>(N, hc, A, reinterpret_cast<const cT*>(a.F), a.coeffs);
+  *launches += 2;
+}
+
+void run_quadrature(const QuadArgs& a, bool mixed, cudaStream_t s, int64_t* launches) {
+  if (mixed)
+    launch_quad<float>(a, a.g->W32, a.g->A32, s, launches);
+  else
+    launch_quad<double>(a, a.g->W64, a.g->A64, s, launches);
+}
+
+}  // namespace hamls

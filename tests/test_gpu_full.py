@@ -1,0 +1,108 @@
+"""Parity at the workloads' full sizes (GPU only).
+
+* N=128, K=3, M=200k tracks + holes: the whole oracle runs (about 30 s);
+  FP64 coefficients within 1e-10, mixed within 1.05x of the oracle's error
+  against the known truth.
+* N=512, K=3, M=4M (the benchmark's workload and launch configuration): the
+  oracle evaluates a seeded sample of grid nodes one by one; the GPU's MLS
+  values there must match, and the mixed form's error against the truth must
+  stay within 1.05x of the FP64 form's."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from hamls_synth import SplitMix64, workload
+from hamls_synth.gen import coeff_norm2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2609_39200_b300 as h
+    h.lib()
+    return h
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def truth_error(c_packed, truth, N):
+    """Relative L2 error (eq. relative_error_S2) against the truth coefficients,
+    by Parseval: degrees <= N compared, degrees > N of the truth count as error."""
+    Lt = truth.shape[0] - 1
+    t = np.zeros((max(N, Lt) + 1, max(N, Lt) + 1), complex)
+    t[:Lt + 1, :Lt + 1] = np.tril(truth)
+    a = O.unpack_coeffs(c_packed, N)
+    diff = t.copy()
+    diff[:N + 1, :N + 1] -= a
+    d2 = np.sum(np.abs(diff[:, 0]) ** 2) + 2 * np.sum(np.abs(diff[:, 1:]) ** 2)
+    return float(np.sqrt(d2 / coeff_norm2(truth)))
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    w = workload("s2_n128_k3_m200k", xp=torch, device="cuda")
+    r = O.hamls(w.nodes, w.values, w.N, w.K, O.Params())
+    return w, r
+
+
+def test_n128_fp64_matches_oracle(h, cfg2):
+    w, r = cfg2
+    with h.Plan(dev(w.nodes), w.N, w.K) as p:
+        c = h.to_complex(p.fit(dev(w.values)))
+        g = p.debug_grid()
+        p.sync(120000)
+    f = g["f"].cpu().numpy()
+    fo = r.fgrid.astype(float)
+    assert np.max(np.abs(f - fo)) < 1e-9 * np.max(np.abs(fo))
+    assert np.linalg.norm(c - r.coeffs) / np.linalg.norm(r.coeffs) < 1e-10
+
+
+def test_n128_mixed_error_bar(h, cfg2):
+    w, r = cfg2
+    with h.Plan(dev(w.nodes), w.N, w.K, precision="mixed") as p:
+        c = h.to_complex(p.fit(dev(w.values)))
+        p.sync(120000)
+    e_or = truth_error(r.coeffs, w.truth, w.N)
+    e_mx = truth_error(c, w.truth, w.N)
+    assert e_mx <= 1.05 * e_or, (e_mx, e_or)
+    assert np.linalg.norm(c - r.coeffs) / np.linalg.norm(r.coeffs) < 1e-3
+
+
+@pytest.fixture(scope="module")
+def cfg3():
+    return workload("s2_n512_k3_m4m", xp=torch, device="cuda")
+
+
+def test_n512_sampled_grid_values_and_error_bar(h, cfg3):
+    w = cfg3
+    x, y = dev(w.nodes), dev(w.values)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        with h.Plan(x, w.N, w.K, precision=prec) as p:
+            c = h.to_complex(p.fit(y))
+            g = p.debug_grid()
+            p.sync(600000)
+            res[prec] = (c, {k: v.cpu().numpy() for k, v in g.items()}, p.stats())
+    MQ = (w.N + 1) * (2 * w.N + 2)
+    rng = SplitMix64(2024)
+    sample = np.unique((rng.uniform(160) * MQ).astype(np.int64))
+    # the heaviest and the most regularised nodes as well
+    g64 = res["fp64"][1]
+    sample = np.unique(np.concatenate([sample, np.argsort(-g64["count"])[:12], np.argsort(-g64["chi"])[:12]]))
+    f, sel, sup, chi, taut, ndrop, grid = O.mls_grid_values(w.nodes, w.values, w.N, w.K, O.Params(), subset=sample)
+    fo = f.astype(float)
+    scale = np.max(np.abs(g64["f"]))
+    assert np.max(np.abs(g64["f"][sample] - fo)) < 1e-9 * scale
+    assert np.array_equal(g64["count"][sample], sup.count)
+    gm = res["mixed"][1]
+    assert np.max(np.abs(gm["f"][sample] - fo)) < 1e-3 * scale
+    e64 = truth_error(res["fp64"][0], w.truth, w.N)
+    emx = truth_error(res["mixed"][0], w.truth, w.N)
+    assert emx <= 1.05 * e64, (emx, e64)
+    assert res["fp64"][2]["min_n"] >= O.dim_tan(w.K)
