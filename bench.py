@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Benchmark of the HAMLS hot path on S^2: fits/s at N=512, K=3, M=4,000,000.
+
+One step = one whole fit of one synthetic input: the node-dependent plan
+stage (cell keys, radix sort, runs, auxiliary k-NN, Shepard support radius,
+neighbour counts, work ordering; hamls_replan) and the value-dependent stage
+(value staging, MLS at all 526,338 grid nodes, ring FFT, Legendre quadrature;
+hamls_fit). Inputs are resident in device memory when a step starts; a
+256 MiB buffer is written between timed steps to flush the 126 MB L2. Each
+step is timed with CUDA events on the plan's stream.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "S^2 N=512 M=4M fits/s & p99 latency, mixed vs FP64 GPU at equal L2 error"
+WORKLOAD = "s2_n512_k3_m4m"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=48, help="grid nodes the oracle evaluates for the CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the FP64 form, e2e and CPU baseline (profiling)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_baseline(w, sample: int, seed: int = 7):
+    """Time the CPU oracle, as it stands, on a bounded sample of the workload:
+    its neighbour structure over all M nodes, the MLS at `sample` seeded grid
+    nodes (with the auxiliary k-NN they need) and the full quadrature step;
+    extrapolate to one whole fit."""
+    import oracle as O
+    from hamls_synth import SplitMix64
+
+    N, K = w.N, w.K
+    MQ = (N + 1) * (2 * N + 2)
+    sel = np.unique((SplitMix64(seed).uniform(sample) * MQ).astype(np.int64))
+    p = O.Params()
+    t0 = time.perf_counter()
+    nodes = O.NodeSet(w.nodes)
+    grid = O.quad_grid(N)
+    t1 = time.perf_counter()
+    aux = O.fibonacci_points(2 * MQ)            # auxiliary grid and its tree, built once per fit
+    O.cKDTree(aux)
+    t_aux = time.perf_counter() - t1
+    t1 = time.perf_counter()
+    sup = O.support_radius(nodes, grid.xyz, K, p, subset=sel)   # rebuilds the auxiliary grid once
+    for jj, j in enumerate(sel):
+        idx = nodes.ball(grid.xyz[j], sup.rho2[jj])
+        O.mls_at(grid.xyz_ld[j], w.nodes[idx], w.values[idx], sup.delta[jj], K, p)
+    t2 = time.perf_counter()
+    O.quadrature(np.zeros(MQ), grid)
+    t3 = time.perf_counter()
+    per_node = max(0.0, (t2 - t1) - t_aux) / len(sel)
+    per_fit = (t1 - t0) + t_aux + per_node * MQ + (t3 - t2)
+    return {"value": 1.0 / per_fit, "unit": "fits/s", "cores": 1, "kind": "oracle",
+            "sample": (f"k-d tree over all {w.M} nodes and the grid ({t1 - t0 - t_aux:.2f} s) and the "
+                       f"auxiliary grid ({t_aux:.2f} s), once; support radius and MLS at {len(sel)} seeded grid "
+                       f"nodes of {MQ} ({t2 - t1 - t_aux:.2f} s, scaled to all {MQ}); full quadrature step "
+                       f"({t3 - t2:.2f} s); numpy/scipy, one host thread"),
+            "seconds": t3 - t0}
+
+
+def run_reference(args):
+    from hamls_synth import workload
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(WORKLOAD)
+    steps = []
+    for _ in range(args.warmup + args.steps):
+        steps.append(oracle_baseline(w, max(8, args.cpu_sample // 4)))
+    timed = steps[args.warmup:]
+    v = float(np.mean([s["value"] for s in timed]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "fits/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": w.N, "K": w.K, "M": w.M},
+            "cpu_baseline": {"value": v, "unit": "fits/s", "cores": 1, "kind": "oracle",
+                             "sample": timed[-1]["sample"]},
+            "e2e": {"value": v, "unit": "fits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv",
+                                       "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.p is None or not os.path.exists(self.path):
+            return None
+        rows = [l.strip().split(", ") for l in open(self.path) if l.strip() and not l.startswith("index")]
+        if not rows:
+            return None
+        mhz = [float(r[1].split()[0]) for r in rows if len(r) > 2]
+        mx = [float(r[2].split()[0]) for r in rows if len(r) > 2]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(mhz)), "sm_max_mhz": max(mx), "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+
+    import paper_2609_39200_b300 as h
+    from hamls_synth import workload
+    from hamls_synth.gen import coeff_norm2
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    h.lib()
+
+    # CPU baseline first (rank 0, N=1), before any GPU work
+    w = workload(WORKLOAD, fit_index=rank, xp=torch, device=dev)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
+        cpu = oracle_baseline(w, args.cpu_sample)
+        cpu.pop("seconds", None)
+
+    x = torch.tensor(w.nodes, device=dev)
+    y = torch.tensor(w.values, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)    # 256 MiB > L2
+    stream = torch.cuda.current_stream(dev)
+    ncoef = (w.N + 1) * (w.N + 2) // 2
+
+    def timed_steps(plan, nodes, values, out, steps, warmup, collect=False):
+        plan.set_timing(True)
+        times, mls, stage_sum = [], [], {}
+        for i in range(warmup + steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if i == warmup:
+                plan.launch_count(reset=True)
+            e0.record(stream)
+            plan.replan(nodes)
+            plan.fit(values, out=out)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= warmup:
+                times.append(e0.elapsed_time(e1))
+                st = plan.stage_times()
+                mls.append(st["mls"])
+                for k, v in st.items():
+                    stage_sum[k] = stage_sum.get(k, 0.0) + v
+        launches = plan.launch_count()
+        plan.sync(600000)
+        return np.array(times), np.array(mls), {k: v / steps for k, v in stage_sum.items()}, launches
+
+    # ---- mixed form (the headline)
+    out = torch.empty((ncoef, 2), dtype=torch.float64, device=dev)
+    plan = h.Plan(x, w.N, w.K, precision="mixed")
+    plan.sync(600000)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        times, mls, stages, launches = timed_steps(plan, x, y, out, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    stats = plan.stats()
+    c_mixed = h.to_complex(out)
+    total_ms = float(times.sum())
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # ---- e2e: host buffers through the C ABI, copies inside the timed region
+    e2e = None
+    if not args.quick:
+        xh = torch.tensor(w.nodes).pin_memory()
+        yh = torch.tensor(w.values).pin_memory()
+        oh = torch.empty((ncoef, 2), dtype=torch.float64).pin_memory()
+        et, _, _, _ = timed_steps(plan, xh, yh, oh, max(3, args.steps // 2), 2)
+        e2e = {"value": world * len(et) / (float(et.sum()) / 1000.0), "unit": "fits/s",
+               "h2d_bytes_per_step": int(xh.numel() * 8 + yh.numel() * 8), "d2h_bytes_per_step": int(oh.numel() * 8),
+               "ms_per_step": float(et.mean())}
+    plan.close()
+
+    # ---- FP64 form (the comparison)
+    fp64 = None
+    c64 = None
+    if not args.quick and args.fp64_steps > 0:
+        out64 = torch.empty((ncoef, 2), dtype=torch.float64, device=dev)
+        p64 = h.Plan(x, w.N, w.K, precision="fp64")
+        t64, m64, st64, _ = timed_steps(p64, x, y, out64, args.fp64_steps, 1)
+        c64 = h.to_complex(out64)
+        fp64 = {"value": world * len(t64) / (float(t64.sum()) / 1000.0), "unit": "fits/s",
+                "ms_per_step": float(t64.mean()), "mls_ms": float(m64.mean()),
+                "stage_ms": {k: round(v, 4) for k, v in st64.items()}}
+        p64.close()
+
+    # ---- accuracy against the known truth (eq. relative_error_S2, by Parseval)
+    def truth_err(c):
+        import oracle as O   # packing helpers only
+        N = w.N
+        Lt = w.truth.shape[0] - 1
+        t = np.zeros((max(N, Lt) + 1,) * 2, complex)
+        t[:Lt + 1, :Lt + 1] = np.tril(w.truth)
+        t[:N + 1, :N + 1] -= O.unpack_coeffs(c, N)
+        d2 = np.sum(np.abs(t[:, 0]) ** 2) + 2 * np.sum(np.abs(t[:, 1:]) ** 2)
+        return float(math.sqrt(d2 / coeff_norm2(w.truth)))
+
+    l2 = {"mixed": truth_err(c_mixed)}
+    if c64 is not None:
+        l2["fp64"] = truth_err(c64)
+        l2["ratio_mixed_over_fp64"] = l2["mixed"] / l2["fp64"]
+        l2["mixed_vs_fp64_coeff_rel"] = float(np.linalg.norm(c_mixed - c64) / np.linalg.norm(c64))
+
+    # ---- roofline of the dominant kernel (the MLS kernel)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    MQ = stats["grid_nodes"]
+    mls_s = float(mls.mean()) / 1000.0
+    alg_bytes = stats["sum_n"] * 16 + MQ * (8 + 8 + 8 + 4)    # gathered FP32 (x,y,z,y) records + delta, rho2, f, order
+    achieved = alg_bytes / mls_s / 1e9
+    roof = {"bound": "hbm", "kernel": "mls_kernel<3,mixed>", "achieved": achieved, "peak": hbm_peak,
+            "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "algorithmic_bytes_per_launch": int(alg_bytes), "mls_ms": float(mls.mean())}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "fits/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": w.N, "K": w.K, "M": w.M, "grid_nodes": MQ,
+                           "precision": "mixed", "parallelism": f"replicas x{world}" if world > 1 else "single",
+                           "l2": "256 MiB write between timed steps"},
+                "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
+                "grid_nodes_per_s": value * MQ,
+                "stage_ms": {k: round(v, 4) for k, v in stages.items()},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk.summary(), "fp64_form": fp64, "l2_error": l2,
+                "mls_stats": {k: stats[k] for k in ("sum_n", "min_n", "max_n", "n_regularized", "n_guarded",
+                                                    "n_fp64_redo", "n_dropped")}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

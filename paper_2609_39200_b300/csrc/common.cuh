@@ -120,44 +120,67 @@ __device__ __forceinline__ float zeta_to_z(float zeta) {
 // Geodesic cap of radius r around a unit vector q, prepared for candidate
 // enumeration in FP32. Every margin enlarges the enumerated set; the caller
 // decides membership with its own exact test.
+//
+// The longitude half-width of the cap at colatitude theta follows from the
+// spherical law of cosines; written as
+//   cos(dphi) = 1 - 2 sin((r + dt)/2) sin((r - dt)/2) / (sin(theta) sin(theta_q)),
+// dt = theta - theta_q, it has no cancellation near the poles or near the
+// cap's rim. Band edges are colatitudes theta = 2 asin((1 - zeta)/sqrt 2)
+// (north) and pi - 2 asin((1 + zeta)/sqrt 2) (south), exact inverses of zeta(z).
 struct Cap {
-  float zq, sq, cph, sph;   // cos/sin colatitude, cos/sin longitude of q
-  float cr;                 // cos r
-  float zlo, zhi;           // z extent of the cap, widened
-  float cstar;              // cos of the largest longitude half-width
-  int polar;                // enumerate whole bands (q at a pole, or r >= pi/2)
+  float th_q, s_q;          // colatitude of q and its sine
+  float cph, sph;           // cos/sin longitude of q
+  float r;                  // radius (widened)
+  float zlo, zhi;           // z extent of the cap, widened (band index range)
+  float th_star, cstar;     // colatitude of the widest longitude extent, cos of that half-width
+  int north, south;         // the cap contains the north / south pole
+  int polar;                // enumerate whole bands (q at a pole, or a cap beyond ~86 degrees)
 };
 
 __device__ __forceinline__ Cap make_cap(double qx, double qy, double qz, double r) {
+  const float PI_F = 3.14159265f;
   Cap c;
-  float fr = fminf((float)r * (1.f + 2e-5f) + 2e-6f, 3.14159265f);
-  float cr, sr;
-  sincosf(fr, &sr, &cr);
-  double sq64 = sqrt(qx * qx + qy * qy);
-  c.zq = (float)qz;
-  c.sq = (float)sq64;
-  c.cr = cr;
-  if (sq64 > 1e-12) {
-    c.cph = (float)(qx / sq64);
-    c.sph = (float)(qy / sq64);
+  // FP32 is enough here: rounding q moves it by < 1e-7 rad, far inside the widening of r
+  const float fx = (float)qx, fy = (float)qy, fz = (float)qz;
+  const float sq = sqrtf(fx * fx + fy * fy);
+  c.th_q = atan2f(sq, fz);
+  c.s_q = sq;
+  if (sq > 1e-12f) {
+    c.cph = fx / sq;
+    c.sph = fy / sq;
   } else {
     c.cph = 1.f;
     c.sph = 0.f;
   }
-  c.polar = (c.sq < 1e-6f) || (cr <= 1e-4f);
-  float zhi = (c.zq >= cr) ? 1.f : c.zq * cr + c.sq * sr;
-  float zlo = (-c.zq >= cr) ? -1.f : c.zq * cr - c.sq * sr;
-  c.zhi = fminf(1.f, zhi + 4e-6f);
-  c.zlo = fmaxf(-1.f, zlo - 4e-6f);
-  float ratio = sr / fmaxf(c.sq, 1e-30f);
-  c.cstar = (ratio >= 1.f) ? -1.f : sqrtf(1.f - ratio * ratio);
+  c.r = fminf((float)r * (1.f + 2e-5f) + 2e-6f, PI_F);
+  c.north = c.th_q <= c.r;
+  c.south = (PI_F - c.th_q) <= c.r;
+  c.polar = (c.s_q < 1e-6f) || (c.r >= 1.5f);
+  c.zhi = c.north ? 1.f : fminf(1.f, cosf(c.th_q - c.r) + 4e-6f);
+  c.zlo = c.south ? -1.f : fmaxf(-1.f, cosf(c.th_q + c.r) - 4e-6f);
+  const float ratio = sinf(c.r) / fmaxf(c.s_q, 1e-30f);
+  if (ratio < 1.f && !c.polar) {
+    c.cstar = sqrtf(1.f - ratio * ratio);
+    c.th_star = acosf(fminf(1.f, fmaxf(-1.f, cosf(c.th_q) / cosf(c.r))));
+  } else {
+    c.cstar = -1.f;
+    c.th_star = -1.f;
+  }
   return c;
 }
 
-// cos of the longitude half-width of the cap at height z
-__device__ __forceinline__ float cap_cos_halfwidth(const Cap& c, float z) {
-  float den = sqrtf(fmaxf(0.f, 1.f - z * z)) * c.sq;
-  return den > 1e-20f ? (c.cr - z * c.zq) / den : -1.f;
+__device__ __forceinline__ float theta_of_zeta(float zeta) {
+  return zeta >= 0.f ? 2.f * asinf((1.f - zeta) * 0.70710678f)
+                     : 3.14159265f - 2.f * asinf((1.f + zeta) * 0.70710678f);
+}
+
+// cos of the cap's longitude half-width at colatitude th (inside the cap's
+// colatitude range); -1 when the geometry degenerates (whole band)
+__device__ __forceinline__ float cap_cos_halfwidth(const Cap& c, float th) {
+  const float den = sinf(th) * c.s_q;
+  if (!(den > 1e-12f)) return -1.f;
+  const float dt = th - c.th_q;
+  return 1.f - 2.f * sinf(0.5f * (c.r + dt)) * sinf(0.5f * (c.r - dt)) / den;
 }
 
 // The (at most two) contiguous runs of sorted points of band b that can lie
@@ -167,46 +190,44 @@ __device__ __forceinline__ void band_runs(const Cells& g, const Cap& c, int b, u
   n0 = n1 = 0;
   s0 = s1 = 0;
   const int B = g.B, P = g.P;
-  float za = zeta_to_z(-1.f + 2.f * (float)b / (float)B);
-  float zb = zeta_to_z(-1.f + 2.f * (float)(b + 1) / (float)B);
-  if (fmaxf(za, c.zlo) > fminf(zb, c.zhi)) return;       // band outside the cap's z extent
-  // the band's z interval, widened past the FP32 rounding of its edges
-  float lo = fmaxf(za - 1e-6f, c.zlo), hi = fminf(zb + 1e-6f, c.zhi);
+  const float PI_F = 3.14159265f;
+  // band b spans zeta in [-1 + 2b/B, -1 + 2(b+1)/B): colatitudes [th_top, th_bot]
+  const float th_bot = theta_of_zeta(-1.f + 2.f * (float)b / (float)B);
+  const float th_top = theta_of_zeta(-1.f + 2.f * (float)(b + 1) / (float)B);
+  const float lo = fmaxf(th_top - 1e-6f, c.th_q - c.r);
+  const float hi = fminf(th_bot + 1e-6f, c.th_q + c.r);
+  if (lo > hi) return;                                      // band outside the cap's colatitudes
   const uint32_t base = (uint32_t)b * (uint32_t)P;
-  // near a pole the half-width is ill-conditioned in FP32: take the whole band
-  float smin = fminf(sqrtf(fmaxf(0.f, 1.f - lo * lo)), sqrtf(fmaxf(0.f, 1.f - hi * hi)));
-  bool full = c.polar || (smin * c.sq < 1e-2f);
-  float cmin = -1.f;
+  bool full = c.polar || (c.north && lo <= c.r - c.th_q) || (c.south && hi >= 2.f * PI_F - c.r - c.th_q);
   if (!full) {
-    cmin = fminf(cap_cos_halfwidth(c, lo), cap_cos_halfwidth(c, hi));
-    float zs = c.zq / c.cr;
-    if (zs > lo && zs < hi) cmin = fminf(cmin, c.cstar);
-    cmin -= 2e-5f;
+    float cmin = fminf(cap_cos_halfwidth(c, fmaxf(lo, 0.f)), cap_cos_halfwidth(c, fminf(hi, PI_F)));
+    if (c.th_star >= 0.f && c.th_star > lo - 1e-4f && c.th_star < hi + 1e-4f) cmin = fminf(cmin, c.cstar);
+    cmin = cmin - 2e-5f * (1.f - cmin) - 1e-6f;
     full = !(cmin > 0.f);
-  }
-  if (!full) {
-    cmin = fminf(cmin, 1.f);
-    float sd = sqrtf(fmaxf(0.f, 1.f - cmin * cmin));
-    float xa = c.cph * cmin + c.sph * sd, ya = c.sph * cmin - c.cph * sd;   // phi_q - dphi
-    float xb = c.cph * cmin - c.sph * sd, yb = c.sph * cmin + c.cph * sd;   // phi_q + dphi
-    int ca = cell_of_f(xa, ya, P), cb = cell_of_f(xb, yb, P);
-    int lo_c = ca - 1, hi_c = cb + 1;
-    if (ca > cb) hi_c += P;
-    if (hi_c - lo_c + 1 >= P) {
-      full = true;
-    } else if (lo_c < 0) {
-      s0 = g.start[base + lo_c + P];
-      n0 = g.start[base + P] - s0;
-      s1 = g.start[base];
-      n1 = g.start[base + hi_c + 1] - s1;
-    } else if (hi_c >= P) {
-      s0 = g.start[base + lo_c];
-      n0 = g.start[base + P] - s0;
-      s1 = g.start[base];
-      n1 = g.start[base + hi_c - P + 1] - s1;
-    } else {
-      s0 = g.start[base + lo_c];
-      n0 = g.start[base + hi_c + 1] - s0;
+    if (!full) {
+      cmin = fminf(cmin, 1.f);
+      const float sd = sqrtf(fmaxf(0.f, 1.f - cmin * cmin));
+      const float xa = c.cph * cmin + c.sph * sd, ya = c.sph * cmin - c.cph * sd;   // phi_q - dphi
+      const float xb = c.cph * cmin - c.sph * sd, yb = c.sph * cmin + c.cph * sd;   // phi_q + dphi
+      const int ca = cell_of_f(xa, ya, P), cb = cell_of_f(xb, yb, P);
+      int lo_c = ca - 1, hi_c = cb + 1;
+      if (ca > cb) hi_c += P;
+      if (hi_c - lo_c + 1 >= P) {
+        full = true;
+      } else if (lo_c < 0) {
+        s0 = g.start[base + lo_c + P];
+        n0 = g.start[base + P] - s0;
+        s1 = g.start[base];
+        n1 = g.start[base + hi_c + 1] - s1;
+      } else if (hi_c >= P) {
+        s0 = g.start[base + lo_c];
+        n0 = g.start[base + P] - s0;
+        s1 = g.start[base];
+        n1 = g.start[base + hi_c - P + 1] - s1;
+      } else {
+        s0 = g.start[base + lo_c];
+        n0 = g.start[base + hi_c + 1] - s0;
+      }
     }
   }
   if (full) {

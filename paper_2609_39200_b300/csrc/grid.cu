@@ -2,7 +2,7 @@
 //
 // The S^2 product rule of Sec. 2.1: Gauss-Legendre nodes t_k in cos(theta)
 // (N+1 nodes, descending), phi_j = 2 pi j / (2N+2). Gauss-Legendre nodes come
-// from Newton's method on P_{N+1} (three-term recurrence), weights from
+// from Newton's method on P_{N+1} in the colatitude, weights from
 // w = 2 / ((1 - t^2) P'_{N+1}(t)^2).
 //
 // Step 3 on this grid is fhat_l^m = (2 pi/(2N+2)) sum_k w_k Pbar_l^m(t_k) F_k(m)
@@ -16,38 +16,58 @@
 
 namespace hamls {
 
+// P_n and D_n = P_n - P_{n-1} at t = cos(theta) = 1 - u, u = 2 sin^2(theta/2),
+// by the three-term recurrence rewritten on differences:
+//   D_{k+1} = (k D_k - (2k+1) u P_k) / (k+1),  P_{k+1} = P_k + D_{k+1},
+// which has no cancellation near t = 1 (the poles).
+__device__ void legendre_pd(int n, double u, double& P, double& D) {
+  double p = 1.0 - u, d = -u;
+  for (int k = 1; k < n; ++k) {
+    d = (k * d - (2 * k + 1) * u * p) / (k + 1);
+    p += d;
+  }
+  P = p;
+  D = d;
+}
+
+// Gauss-Legendre nodes by Newton's method on P_{N+1}(cos theta) in the
+// colatitude theta (northern half; the southern half is the exact mirror
+// t_{N-k} = -t_k, w_{N-k} = w_k). dP/dtheta = n (D_n - u P_n) / sin(theta) and
+// w = 2 / ((1 - t^2) P'(t)^2) = 2 sin^2(theta) / (n (D_n - u P_n))^2.
 __global__ void gl_kernel(int N, double* t_out, double* w_out, double* s_out) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k > N) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = N + 1;
-  double t = cospi((k + 0.75) / (n + 0.5));
-  double p0 = 1.0, p1 = t;
-  for (int it = 0; it < 100; ++it) {
-    p0 = 1.0;
-    p1 = t;
-    for (int j = 2; j <= n; ++j) {
-      double p2 = ((2 * j - 1) * t * p1 - (j - 1) * p0) / j;
-      p0 = p1;
-      p1 = p2;
-    }
-    if (n == 1) p0 = 1.0;
-    double dp = n * (t * p1 - p0) / (t * t - 1.0);
-    double dt = p1 / dp;
-    t -= dt;
-    if (fabs(dt) < 1e-17) break;
+  if (k >= (n + 1) / 2) return;
+  const bool middle = (n & 1) && k == (n - 1) / 2;
+  double th = middle ? 0.5 * 3.14159265358979323846 : 3.14159265358979323846 * (k + 0.75) / (n + 0.5);
+  double P, D, u, sh;
+  for (int it = 0; it < 100 && !middle; ++it) {
+    sh = sin(0.5 * th);
+    u = 2.0 * sh * sh;
+    legendre_pd(n, u, P, D);
+    const double dth = P * sin(th) / (n * (D - u * P));
+    th -= dth;
+    if (fabs(dth) <= 1e-17 * th) break;
   }
-  p0 = 1.0;
-  p1 = t;
-  for (int j = 2; j <= n; ++j) {
-    double p2 = ((2 * j - 1) * t * p1 - (j - 1) * p0) / j;
-    p0 = p1;
-    p1 = p2;
+  sh = sin(0.5 * th);
+  u = middle ? 1.0 : 2.0 * sh * sh;
+  legendre_pd(n, u, P, D);
+  double st, ct;
+  sincos(th, &st, &ct);
+  if (middle) {
+    st = 1.0;
+    ct = 0.0;
   }
-  if (n == 1) p0 = 1.0;
-  double dp = n * (t * p1 - p0) / (t * t - 1.0);
-  t_out[k] = t;
-  w_out[k] = 2.0 / ((1.0 - t * t) * dp * dp);
-  s_out[k] = sqrt((1.0 - t) * (1.0 + t));
+  const double g = n * (D - u * P);
+  const double w = 2.0 * st * st / (g * g);
+  t_out[k] = ct;
+  w_out[k] = w;
+  s_out[k] = st;
+  if (!middle) {
+    t_out[N - k] = -ct;
+    w_out[N - k] = w;
+    s_out[N - k] = st;
+  }
 }
 
 __global__ void phi_kernel(int L, double* cphi, double* sphi, double2* W64, float2* W32) {
@@ -113,7 +133,7 @@ __global__ void legendre_gen_kernel(int N, int hc, const double* __restrict__ t,
 
 void build_grid_tables(GridTables& g, bool want32, bool want64, cudaStream_t s, int64_t* launches) {
   const int N = g.N, L = 2 * N + 2;
-  gl_kernel<<<(N + 1 + 127) / 128, 128, 0, s>>>(N, g.t, g.w, g.s);
+  gl_kernel<<<(N + 2) / 2 / 128 + 1, 128, 0, s>>>(N, g.t, g.w, g.s);
   phi_kernel<<<(L + 255) / 256, 256, 0, s>>>(L, g.cphi, g.sphi, g.W64, want32 ? g.W32 : nullptr);
   rec_kernel<<<N + 1, 256, 0, s>>>(N, g.a_rec, g.b_rec);
   dim3 grid((g.hc + 63) / 64, N + 1);

@@ -56,7 +56,7 @@ __device__ double knn_nth(const Cells& g, double qx, double qy, double qz, int n
     } else if (have_lo) {
       r = fmin(2.0 * r, PI);
     } else {
-      if (r < 1e-9) break;
+      if (r < 1e-6) break;
       r = 0.5 * r;
     }
   }
@@ -118,7 +118,13 @@ __device__ double knn_nth(const Cells& g, double qx, double qy, double qz, int n
     const double sr = sin(0.5 * r);
     const double rho2 = 4.0 * sr * sr;
     if (nth < rho2 || r >= PI) return nth;
-    r = fmin(r * 1.25, PI);
+    if (nth < 1e300) {
+      // n candidates lie within the chord sqrt(nth): the cap through the
+      // n-th of them holds at least n nodes, so the next scan is valid
+      r = fmin(PI, fmax(1.25 * r, geodesic_from_chord2(nth) * (1.0 + 1e-7) + 1e-12));
+    } else {
+      r = fmin(PI, fmax(2.0 * r, 0.25 * r0));
+    }
   }
   *failed = true;
   return __longlong_as_double(0x7ff0000000000000ll);
