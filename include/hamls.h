@@ -88,6 +88,10 @@ typedef struct {
   int64_t grid_nodes;     /* M_Q */
   int64_t aux_points;     /* size of the auxiliary grid */
   int32_t bands, cells;   /* neighbour structure: latitude bands and cells per band */
+  int64_t knn_candidates; /* auxiliary k-NN: candidates streamed by the tile search */
+  int64_t knn_insertions; /* auxiliary k-NN: per-point heap insertions */
+  int64_t knn_lane_fallbacks;   /* auxiliary points resolved by a single-point search */
+  int64_t knn_exact_fallbacks;  /* single-point searches that needed all-FP64 distances */
 } hamls_fit_stats;
 
 /* Fill *p with the defaults listed in hamls_params. */
@@ -159,6 +163,28 @@ hamls_status hamls_stage_times(hamls_plan_t plan, float* ms, int capacity, int* 
 /* Number of kernel launches the library made on the plan's behalf since the
  * last reset (reset with reset != 0). */
 int64_t hamls_launch_count(hamls_plan_t plan, int reset);
+
+/*
+ * hamls_cells_noalloc - the cell-list build of hamls_plan (integer cell keys,
+ * stable radix sort, CSR runs; the same output as hamls_debug_cells for the
+ * same bands/cells) for callers that cannot allocate device memory. The paper
+ * has no counterpart: this is a service of the library.
+ *   nodes_xyz    M x 3 doubles, row-major unit vectors, device memory
+ *   M            1 <= M <= 1,048,576 (larger M returns HAMLS_ERR_CAPACITY)
+ *   bands,cells  key shape: bands even in [2, 4096], cells a multiple of 4 in [4, 8192]
+ *   keys_sorted  M uint32 (device): sorted cell keys
+ *   perm         M uint32 (device): sorted position -> original node index (stable)
+ *   cell_start   bands*cells + 1 uint32 (device): first sorted position of each cell
+ * It calls no allocator: the sort's scratch is a static device array of about
+ * 8.3 MiB that every GPU loading the library keeps until the process exits.
+ * The first call on a device looks up that array's device address (once per
+ * device); make that first call before any stream capture. All calls share
+ * the one array, so calls that overlap on the GPU (other streams, other host
+ * threads) race: serialise them. Nodes that are not unit vectors are filed in
+ * the north-pole cell; no status is reported for them.
+ */
+hamls_status hamls_cells_noalloc(const double* nodes_xyz, int64_t M, int bands, int cells, uint32_t* keys_sorted,
+                                 uint32_t* perm, uint32_t* cell_start, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

@@ -46,7 +46,9 @@ class FitStats(ctypes.Structure):
     _fields_ = [("sum_n", ctypes.c_int64), ("min_n", ctypes.c_int64), ("max_n", ctypes.c_int64),
                 ("n_regularized", ctypes.c_int64), ("n_guarded", ctypes.c_int64), ("n_fp64_redo", ctypes.c_int64),
                 ("n_dropped", ctypes.c_int64), ("grid_nodes", ctypes.c_int64), ("aux_points", ctypes.c_int64),
-                ("bands", ctypes.c_int32), ("cells", ctypes.c_int32)]
+                ("bands", ctypes.c_int32), ("cells", ctypes.c_int32), ("knn_candidates", ctypes.c_int64),
+                ("knn_insertions", ctypes.c_int64), ("knn_lane_fallbacks", ctypes.c_int64),
+                ("knn_exact_fallbacks", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -72,6 +74,7 @@ _SIGS = {
     "hamls_debug_aux": (_I, [_P, _P, _P, _P]),
     "hamls_debug_quadrature": (_I, [_P, _P, _P, _P]),
     "hamls_debug_gl": (_I, [_P, _P, _P, _P]),
+    "hamls_cells_noalloc": (_I, [_P, _I64, _I, _I, _P, _P, _P, _P]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -258,6 +261,14 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def cells_noalloc(nodes: torch.Tensor, bands: int, cells: int, keys_sorted: torch.Tensor, perm: torch.Tensor,
+                  cell_start: torch.Tensor, stream=None):
+    """The cell-list build without device allocation (hamls_cells_noalloc):
+    all arguments are caller-owned device tensors (int32 views of uint32)."""
+    _check(lib().hamls_cells_noalloc(_ptr(nodes), int(nodes.shape[0]), int(bands), int(cells), _ptr(keys_sorted),
+                                     _ptr(perm), _ptr(cell_start), _stream(stream)), "hamls_cells_noalloc")
 
 
 def to_complex(coeffs: torch.Tensor) -> np.ndarray:

@@ -57,27 +57,80 @@ __global__ void __launch_bounds__(SORT_THREADS) radix_hist(const uint32_t* __res
   counts[(size_t)tid * nblocks + blockIdx.x] = h[tid];
 }
 
-// exclusive scan of `len` counts in place, one block of 1024 threads
-__global__ void __launch_bounds__(1024) scan_exclusive(uint32_t* __restrict__ a, int len) {
-  __shared__ uint32_t part[1024];
-  const int tid = threadIdx.x;
-  const int per = (len + 1023) / 1024;
-  const int lo = min(tid * per, len), hi = min(lo + per, len);
-  uint32_t s = 0;
-  for (int i = lo; i < hi; ++i) s += a[i];
-  part[tid] = s;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    uint32_t t = tid >= o ? part[tid - o] : 0;
-    __syncthreads();
-    part[tid] += t;
-    __syncthreads();
+// Exclusive scan of `len` counts in place: block sums of 1024-entry tiles,
+// one block scans the sums, then every tile scans itself from its offset.
+constexpr int SCAN_TILE = 1024;
+
+int scan_partials(int n) { return (256 * radix_blocks(n) + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+__device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t* sh, uint32_t& total) {
+  // inclusive scan over 256 threads (8 warps)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += t;
   }
-  uint32_t run = part[tid] - s;
-  for (int i = lo; i < hi; ++i) {
-    uint32_t v = a[i];
-    a[i] = run;
-    run += v;
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < 8 ? sh[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      uint32_t t = __shfl_up_sync(FULL, w, o);
+      if (lane >= o) w += t;
+    }
+    if (lane < 8) sh[8 + lane] = w;
+  }
+  __syncthreads();
+  total = sh[15];
+  const uint32_t r = x + (warp > 0 ? sh[8 + warp - 1] : 0u);
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(256) scan_tile_sums(const uint32_t* __restrict__ a, int len,
+                                                      uint32_t* __restrict__ part) {
+  __shared__ uint32_t sh[16];
+  const int base = blockIdx.x * SCAN_TILE;
+  uint32_t s = 0;
+#pragma unroll
+  for (int r = 0; r < SCAN_TILE / 256; ++r) {
+    const int i = base + r * 256 + threadIdx.x;
+    if (i < len) s += a[i];
+  }
+  uint32_t total;
+  block_scan_256(s, sh, total);
+  if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(256) scan_sums(uint32_t* __restrict__ part, int np) {
+  __shared__ uint32_t sh[16];
+  uint32_t carry = 0;
+  for (int b0 = 0; b0 < np; b0 += 256) {
+    const int i = b0 + threadIdx.x;
+    const uint32_t v = i < np ? part[i] : 0u;
+    uint32_t total;
+    const uint32_t incl = block_scan_256(v, sh, total);
+    if (i < np) part[i] = carry + incl - v;
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(256) scan_tiles(uint32_t* __restrict__ a, int len,
+                                                  const uint32_t* __restrict__ part) {
+  __shared__ uint32_t sh[16];
+  const int base = blockIdx.x * SCAN_TILE;
+  uint32_t carry = part[blockIdx.x];
+#pragma unroll
+  for (int r = 0; r < SCAN_TILE / 256; ++r) {
+    const int i = base + r * 256 + threadIdx.x;
+    const uint32_t v = i < len ? a[i] : 0u;
+    uint32_t total;
+    const uint32_t incl = block_scan_256(v, sh, total);
+    if (i < len) a[i] = carry + incl - v;
+    carry += total;
   }
 }
 
@@ -135,10 +188,14 @@ bool radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32
   for (int shift = 0; shift < bits; shift += 8) {
     const int w = min(8, bits - shift);
     const uint32_t mask = (1u << w) - 1u;
+    const int len = 256 * nb, nt = (len + SCAN_TILE - 1) / SCAN_TILE;
+    uint32_t* part = counts + len;
     radix_hist<<<nb, SORT_THREADS, 0, s>>>(ki, n, shift, mask, counts, nb);
-    scan_exclusive<<<1, 1024, 0, s>>>(counts, 256 * nb);
+    scan_tile_sums<<<nt, 256, 0, s>>>(counts, len, part);
+    scan_sums<<<1, 256, 0, s>>>(part, nt);
+    scan_tiles<<<nt, 256, 0, s>>>(counts, len, part);
     radix_scatter<<<nb, SORT_THREADS, 0, s>>>(ki, vi, ko, vo, counts, n, shift, mask, nb);
-    *launches += 3;
+    *launches += 5;
     uint32_t* t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
     alt = !alt;
@@ -227,6 +284,28 @@ void build_cells(const CellBuild& cb, cudaStream_t s, int64_t* launches) {
   ++*launches;
   *cb.perm_out = perm;
   *cb.keys_out = sk;
+}
+
+// A second ordering of already sorted points by a coarser band structure:
+// 32 consecutive points of it form a compact tile.
+void build_tile_order(const double* px, const double* py, const double* pz, int n, int B, int P, uint32_t* keys,
+                      uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* counts,
+                      const uint32_t** order_out, cudaStream_t s, int64_t* launches) {
+  keys_kernel_soa<<<(n + 255) / 256, 256, 0, s>>>(px, py, pz, n, B, P, keys, vals);
+  ++*launches;
+  int bits = 0;
+  while ((1ull << bits) < (unsigned long long)B * P) ++bits;
+  bool alt = radix_sort_pairs(keys, vals, keys_alt, vals_alt, n, bits, counts, s, launches);
+  *order_out = alt ? vals_alt : vals;
+}
+
+void launch_cell_keys(const double* xyz, int n, int B, int P, uint32_t* keys, uint32_t* vals, DevStatus* st,
+                      cudaStream_t s) {
+  keys_kernel<<<(n + 255) / 256, 256, 0, s>>>(xyz, n, B, P, keys, vals, st);
+}
+
+void launch_csr(const uint32_t* sk, int n, int ncells, uint32_t* start, cudaStream_t s) {
+  csr_kernel<<<(n + 1 + 255) / 256, 256, 0, s>>>(sk, n, ncells, start);
 }
 
 void stage_values(const double* y, const uint32_t* perm, int n, double* sy, float4* pf, bool write64,

@@ -25,8 +25,15 @@ int radix_blocks(int n);
 void build_cells(const CellBuild& cb, cudaStream_t s, int64_t* launches);
 bool radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int n, int bits,
                       uint32_t* counts, cudaStream_t s, int64_t* launches);
+int scan_partials(int n);   // scratch words radix_sort_pairs needs after the counts (see cells.cu)
+void launch_cell_keys(const double* xyz, int n, int B, int P, uint32_t* keys, uint32_t* vals, DevStatus* st,
+                      cudaStream_t s);
+void launch_csr(const uint32_t* sk, int n, int ncells, uint32_t* start, cudaStream_t s);
 void stage_values(const double* y, const uint32_t* perm, int n, double* sy, float4* pf, bool write64,
                   DevStatus* st, cudaStream_t s, int64_t* launches);
+void build_tile_order(const double* px, const double* py, const double* pz, int n, int B, int P, uint32_t* keys,
+                      uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* counts,
+                      const uint32_t** order_out, cudaStream_t s, int64_t* launches);
 
 // ------------------------------------------------------------------- grid.cu
 struct GridTables {
@@ -38,6 +45,7 @@ struct GridTables {
   float* A32;
   double2* W64;                 // FFT twiddles exp(-2 pi i j / L), L = 2N+2
   float2* W32;
+  float *tf, *sf, *cpf, *spf;   // FP32 copies of t, s, cphi, sphi (FP32 paths)
   int hc;                       // folded column count
 };
 void build_grid_tables(GridTables& g, bool want32, bool want64, cudaStream_t s, int64_t* launches);
@@ -51,14 +59,20 @@ struct SupportArgs {
   double eps, rho_aux;
   const double *ring_t, *ring_s, *cphi, *sphi;
   double* dn_aux_sorted;        // aux d_n (geodesic), sorted aux order
+  float* dn_aux_f;              // the same in FP32
   double* delta;                // M_Q
   double* rho2;                 // M_Q
+  float* deltaf;                // M_Q, FP32 copies for the FP32 paths
+  float* rho2f;
+  const float *tf, *sf, *cpf, *spf;
   int32_t* count;               // M_Q
   uint8_t* guarded;             // M_Q
   uint32_t* guard_list;         // M_Q
   uint32_t* order_keys;         // M_Q (cost keys)
   uint32_t* order_vals;         // M_Q
   int fp64;                     // 1: FP64 Shepard, 0: FP32
+  const uint32_t* tile_order;   // aux points (sorted positions) in tile order
+  int num_sms;
   DevStatus* st;
 };
 void run_aux_knn(const SupportArgs& a, cudaStream_t s, int64_t* launches);
@@ -79,6 +93,9 @@ struct MlsArgs {
   int N, K;
   const double* delta;
   const double* rho2;
+  const float* deltaf;
+  const float* rho2f;
+  const float *tf, *sf, *cpf, *spf;
   const uint32_t* order;        // grid nodes, heaviest first
   int MQ;
   double* fgrid;
@@ -86,12 +103,13 @@ struct MlsArgs {
   double* tau;
   double chiT, chiF, floor_, fp64_pivot;
   double mu[KMAX + 1];
-  float* redo_mom;              // MIXED: moments of nodes re-solved in FP64
-  uint32_t* redo_node;
+  void* mom;                    // per work-order position: moments (float MIXED, double FP64)
+  uint32_t* redo_list;          // MIXED: work-order positions re-solved in FP64
   DevStatus* st;
   int num_sms;
 };
 void run_mls(const MlsArgs& a, bool mixed, cudaStream_t s, int64_t* launches);
+int mls_moment_slots(int K);
 
 // ------------------------------------------------------------------- quad.cu
 struct QuadArgs {
@@ -102,6 +120,7 @@ struct QuadArgs {
   int radices[32];
   int nrad;
 };
-void run_quadrature(const QuadArgs& a, bool mixed, cudaStream_t s, int64_t* launches);
+// part: 1 = ring FFT, 2 = Legendre contraction, 3 = both
+void run_quadrature(const QuadArgs& a, bool mixed, cudaStream_t s, int64_t* launches, int part = 3);
 
 }  // namespace hamls
