@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=48, help="grid nodes the oracle evaluates for the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the FP64 form, e2e and CPU baseline (profiling)")
+    ap.add_argument("--cache", default=None, help="directory to keep/reuse the generated workload (profiling runs)")
+    ap.add_argument("--fp64-pivot", type=float, default=None, help="mixed form: squared FP32 pivot below which a "
+                    "local solve is redone in FP64 (library default if omitted)")
     return ap.parse_args()
 
 
@@ -148,6 +151,22 @@ class Clocks:
 
 
 # --------------------------------------------------------------------- ours
+def load_workload(cache, rank, torch, dev):
+    """The seeded benchmark workload; with a cache directory, generated once and reused."""
+    from hamls_synth import workload
+    from hamls_synth.gen import Workload
+
+    path = os.path.join(cache, f"{WORKLOAD}_{rank}.npz") if cache else None
+    if path and os.path.exists(path):
+        z = np.load(path, allow_pickle=False)
+        return Workload(WORKLOAD, int(z["N"]), int(z["K"]), int(z["M"]), z["nodes"], z["values"], z["truth"], {})
+    w = workload(WORKLOAD, fit_index=rank, xp=torch, device=dev)
+    if path:
+        os.makedirs(cache, exist_ok=True)
+        np.savez(path, N=w.N, K=w.K, M=w.M, nodes=w.nodes, values=w.values, truth=w.truth)
+    return w
+
+
 def run_ours(args):
     import torch
 
@@ -167,7 +186,7 @@ def run_ours(args):
     h.lib()
 
     # CPU baseline first (rank 0, N=1), before any GPU work
-    w = workload(WORKLOAD, fit_index=rank, xp=torch, device=dev)
+    w = load_workload(args.cache, rank, torch, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         cpu = oracle_baseline(w, args.cpu_sample)
@@ -204,7 +223,8 @@ def run_ours(args):
 
     # ---- mixed form (the headline)
     out = torch.empty((ncoef, 2), dtype=torch.float64, device=dev)
-    plan = h.Plan(x, w.N, w.K, precision="mixed")
+    kw = {} if args.fp64_pivot is None else {"fp64_pivot": args.fp64_pivot}
+    plan = h.Plan(x, w.N, w.K, precision="mixed", **kw)
     plan.sync(600000)
     if dist:
         dist.barrier()
@@ -294,7 +314,9 @@ def run_ours(args):
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk.summary(), "fp64_form": fp64, "l2_error": l2,
                 "mls_stats": {k: stats[k] for k in ("sum_n", "min_n", "max_n", "n_regularized", "n_guarded",
-                                                    "n_fp64_redo", "n_dropped")}}
+                                                    "n_fp64_redo", "n_dropped")},
+                "knn_stats": {k: stats[k] for k in ("aux_points", "knn_candidates", "knn_insertions",
+                                                    "knn_lane_fallbacks", "knn_exact_fallbacks")}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -88,15 +88,19 @@ struct hamls_plan_s {
   uint32_t *akeys, *avals, *akeys_alt, *avals_alt, *astart;
   const uint32_t *aperm = nullptr, *askeys = nullptr;
   double *ax, *ay, *az, *apx, *apy, *apz, *dn_aux;
+  float* dn_auxf;
   float4* apf;
+  uint32_t *tkeys, *tvals, *tkeys_alt, *tvals_alt;
+  const uint32_t* tile_order = nullptr;
   // grid nodes
   double *delta, *rho2, *fgrid, *chi, *tau;
+  float *deltaf, *rho2f;
+  uint32_t* redo_list;
   int32_t* count;
   uint8_t* guarded;
   uint32_t *guard_list, *okeys, *ovals, *okeys_alt, *ovals_alt;
   const uint32_t* order = nullptr;
-  float* redo_mom;
-  uint32_t* redo_node;
+  void* mom;
   void* F;
   double* coeffs;
   // staging of host inputs
@@ -146,12 +150,16 @@ void carve(hamls_plan_s* P) {
   P->g.A32 = P->mixed ? A.take<float>(ncoef * P->g.hc) : nullptr;
   P->g.W64 = A.take<double2>(L);
   P->g.W32 = A.take<float2>(L);
+  P->g.tf = A.take<float>(N + 1);
+  P->g.sf = A.take<float>(N + 1);
+  P->g.cpf = A.take<float>(L);
+  P->g.spf = A.take<float>(L);
   // nodes
   P->keys = A.take<uint32_t>(M);
   P->vals = A.take<uint32_t>(M);
   P->keys_alt = A.take<uint32_t>(M);
   P->vals_alt = A.take<uint32_t>(M);
-  P->counts = A.take<uint32_t>((size_t)256 * radix_blocks(sortmax));
+  P->counts = A.take<uint32_t>((size_t)256 * radix_blocks(sortmax) + scan_partials(sortmax));
   P->start = A.take<uint32_t>((size_t)P->B * P->P + 1);
   P->px = A.take<double>(M);
   P->py = A.take<double>(M);
@@ -173,10 +181,18 @@ void carve(hamls_plan_s* P) {
   P->apy = A.take<double>(Ma);
   P->apz = A.take<double>(Ma);
   P->dn_aux = A.take<double>(Ma);
+  P->dn_auxf = A.take<float>(Ma);
   P->apf = A.take<float4>(Ma);
+  P->tkeys = A.take<uint32_t>(Ma);
+  P->tvals = A.take<uint32_t>(Ma);
+  P->tkeys_alt = A.take<uint32_t>(Ma);
+  P->tvals_alt = A.take<uint32_t>(Ma);
   // grid nodes
   P->delta = A.take<double>(MQ);
   P->rho2 = A.take<double>(MQ);
+  P->deltaf = A.take<float>(MQ);
+  P->rho2f = A.take<float>(MQ);
+  P->redo_list = A.take<uint32_t>(MQ);
   P->fgrid = A.take<double>(MQ);
   P->chi = A.take<double>(MQ);
   P->tau = A.take<double>(MQ);
@@ -187,9 +203,7 @@ void carve(hamls_plan_s* P) {
   P->ovals = A.take<uint32_t>(MQ);
   P->okeys_alt = A.take<uint32_t>(MQ);
   P->ovals_alt = A.take<uint32_t>(MQ);
-  const int NV = dim_tan_host(2 * P->K) + dim_tan_host(P->K);
-  P->redo_mom = P->mixed ? A.take<float>((size_t)MQ * NV) : nullptr;
-  P->redo_node = A.take<uint32_t>(MQ);
+  P->mom = A.take<double>((size_t)MQ * mls_moment_slots(P->K) / (P->mixed ? 2 : 1) + 2);
   P->F = A.take<double2>((size_t)(N + 1) * (N + 1));
   P->coeffs = A.take<double>(2 * ncoef);
   P->in_nodes = A.take<double>((size_t)3 * M);
@@ -250,14 +264,23 @@ SupportArgs support_args(hamls_plan_s* P) {
   a.cphi = P->g.cphi;
   a.sphi = P->g.sphi;
   a.dn_aux_sorted = P->dn_aux;
+  a.dn_aux_f = P->dn_auxf;
   a.delta = P->delta;
   a.rho2 = P->rho2;
+  a.deltaf = P->deltaf;
+  a.rho2f = P->rho2f;
+  a.tf = P->g.tf;
+  a.sf = P->g.sf;
+  a.cpf = P->g.cpf;
+  a.spf = P->g.spf;
   a.count = P->count;
   a.guarded = P->guarded;
   a.guard_list = P->guard_list;
   a.order_keys = P->okeys;
   a.order_vals = P->ovals;
   a.fp64 = P->mixed ? 0 : 1;
+  a.tile_order = P->tile_order;
+  a.num_sms = P->num_sms;
   a.st = P->st;
   return a;
 }
@@ -345,6 +368,13 @@ hamls_status build_static(hamls_plan_s* P, cudaStream_t s) {
   cb.perm_out = &P->aperm;
   cb.keys_out = &P->askeys;
   build_cells(cb, s, &P->launches);
+  // tile order of the auxiliary points for the k-NN: coarse latitude bands of
+  // about sqrt(32) point spacings, then longitude
+  const double spacing = sqrt(4.0 * M_PI / (double)P->M_aux);
+  int bt = 2;
+  while (bt < 4096 && 3.4 / bt > sqrt(32.0) * spacing) bt *= 2;
+  build_tile_order(P->apx, P->apy, P->apz, P->M_aux, bt, 8192, P->tkeys, P->tvals, P->tkeys_alt, P->tvals_alt,
+                   P->counts, &P->tile_order, s, &P->launches);
   return cuda_status(cudaGetLastError());
 }
 
@@ -496,6 +526,12 @@ hamls_status hamls_fit(hamls_plan_t P, const double* values, double* coeffs, cud
   a.K = P->K;
   a.delta = P->delta;
   a.rho2 = P->rho2;
+  a.deltaf = P->deltaf;
+  a.rho2f = P->rho2f;
+  a.tf = P->g.tf;
+  a.sf = P->g.sf;
+  a.cpf = P->g.cpf;
+  a.spf = P->g.spf;
   a.order = P->order;
   a.MQ = P->MQ;
   a.fgrid = P->fgrid;
@@ -506,8 +542,8 @@ hamls_status hamls_fit(hamls_plan_t P, const double* values, double* coeffs, cud
   a.floor_ = P->p.pivot_floor;
   a.fp64_pivot = P->p.fp64_pivot;
   for (int l = 0; l <= KMAX; ++l) a.mu[l] = pow((double)l * (l + 1), P->p.sobolev_s);
-  a.redo_mom = P->redo_mom;
-  a.redo_node = P->redo_node;
+  a.mom = P->mom;
+  a.redo_list = P->redo_list;
   a.st = P->st;
   a.num_sms = P->num_sms;
   stage_begin(P, 5, s);
@@ -523,8 +559,11 @@ hamls_status hamls_fit(hamls_plan_t P, const double* values, double* coeffs, cud
   for (int i = 0; i < P->nrad; ++i) q.radices[i] = P->radices[i];
   q.nrad = P->nrad;
   stage_begin(P, 6, s);
-  run_quadrature(q, P->mixed, s, &P->launches);
+  run_quadrature(q, P->mixed, s, &P->launches, 1);
   stage_end(P, 6, s);
+  stage_begin(P, 7, s);
+  run_quadrature(q, P->mixed, s, &P->launches, 2);
+  stage_end(P, 7, s);
   if (!dev_out) {
     const size_t ncoef = (size_t)(P->N + 1) * (P->N + 2) / 2;
     HAMLS_TRY(cudaMemcpyAsync(coeffs, P->coeffs, ncoef * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -573,6 +612,10 @@ hamls_status hamls_stats(hamls_plan_t P, hamls_fit_stats* out) {
   out->aux_points = P->M_aux;
   out->bands = P->B;
   out->cells = P->P;
+  out->knn_candidates = (int64_t)d.cnt[C_KNN_CAND];
+  out->knn_insertions = (int64_t)d.cnt[C_KNN_INS];
+  out->knn_lane_fallbacks = (int64_t)d.cnt[C_KNN_LANE_FB];
+  out->knn_exact_fallbacks = (int64_t)d.cnt[C_KNN_EXACT_FB];
   return HAMLS_OK;
 }
 

@@ -34,7 +34,7 @@ enum : unsigned {
 
 // device counters
 enum { C_SUM_N = 0, C_MIN_N, C_MAX_N, C_REG, C_GUARD, C_REDO, C_DROP, C_GUARD_LIST, C_REDO_LIST,
-       C_BATCH, C_NCOUNT };
+       C_BATCH, C_TILE, C_KNN_CAND, C_KNN_INS, C_KNN_LANE_FB, C_KNN_EXACT_FB, C_NCOUNT };
 
 struct DevStatus {
   unsigned flags;
@@ -137,11 +137,10 @@ struct Cap {
   int polar;                // enumerate whole bands (q at a pole, or a cap beyond ~86 degrees)
 };
 
-__device__ __forceinline__ Cap make_cap(double qx, double qy, double qz, double r) {
+// FP32 is enough here: rounding q moves it by < 1e-7 rad, far inside the widening of r
+__device__ __forceinline__ Cap make_cap_f(float fx, float fy, float fz, float rf) {
   const float PI_F = 3.14159265f;
   Cap c;
-  // FP32 is enough here: rounding q moves it by < 1e-7 rad, far inside the widening of r
-  const float fx = (float)qx, fy = (float)qy, fz = (float)qz;
   const float sq = sqrtf(fx * fx + fy * fy);
   c.th_q = atan2f(sq, fz);
   c.s_q = sq;
@@ -152,7 +151,7 @@ __device__ __forceinline__ Cap make_cap(double qx, double qy, double qz, double 
     c.cph = 1.f;
     c.sph = 0.f;
   }
-  c.r = fminf((float)r * (1.f + 2e-5f) + 2e-6f, PI_F);
+  c.r = fminf(rf * (1.f + 2e-5f) + 2e-6f, PI_F);
   c.north = c.th_q <= c.r;
   c.south = (PI_F - c.th_q) <= c.r;
   c.polar = (c.s_q < 1e-6f) || (c.r >= 1.5f);
@@ -167,6 +166,10 @@ __device__ __forceinline__ Cap make_cap(double qx, double qy, double qz, double 
     c.th_star = -1.f;
   }
   return c;
+}
+
+__device__ __forceinline__ Cap make_cap(double qx, double qy, double qz, double r) {
+  return make_cap_f((float)qx, (float)qy, (float)qz, (float)r);
 }
 
 __device__ __forceinline__ float theta_of_zeta(float zeta) {
@@ -246,15 +249,22 @@ __device__ __forceinline__ void cap_band_range(const Cells& g, const Cap& c, int
 // the cap. The runs of 32 consecutive bands are concatenated and dealt to the
 // lanes 32 at a time, so consecutive lanes read consecutive points. f(valid,
 // idx) is called by all 32 lanes together (it may use warp intrinsics).
-template <class F>
+//
+// With MIDOUT the bands are visited from the cap centre's band outwards
+// (offsets 0, +1, -1, +2, -2, ...), so candidates arrive roughly nearest
+// first; searches that keep the n nearest then rarely update after a while.
+template <bool MIDOUT = false, class F>
 __device__ __forceinline__ void for_cap_candidates(const Cells& g, const Cap& c, F&& f) {
   const int lane = threadIdx.x & 31;
   int b_lo, b_hi;
   cap_band_range(g, c, b_lo, b_hi);
-  for (int b0 = b_lo; b0 <= b_hi; b0 += 32) {
-    const int b = b0 + lane;
+  const int bc = MIDOUT ? min(max(band_of_f(cosf(c.th_q), g.B), b_lo), b_hi) : b_lo;
+  const int span = MIDOUT ? 2 * max(bc - b_lo, b_hi - bc) + 1 : b_hi - b_lo + 1;
+  for (int k0 = 0; k0 < span; k0 += 32) {
+    const int k = k0 + lane;
+    const int b = MIDOUT ? bc + ((k & 1) ? (k + 1) / 2 : -(k / 2)) : b_lo + k;
     uint32_t s0 = 0, n0 = 0, s1 = 0, n1 = 0;
-    if (b <= b_hi) band_runs(g, c, b, s0, n0, s1, n1);
+    if (k < span && b >= b_lo && b <= b_hi) band_runs(g, c, b, s0, n0, s1, n1);
     const uint32_t len = n0 + n1;
     uint32_t incl = len;
 #pragma unroll

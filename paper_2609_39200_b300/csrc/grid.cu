@@ -34,7 +34,7 @@ __device__ void legendre_pd(int n, double u, double& P, double& D) {
 // colatitude theta (northern half; the southern half is the exact mirror
 // t_{N-k} = -t_k, w_{N-k} = w_k). dP/dtheta = n (D_n - u P_n) / sin(theta) and
 // w = 2 / ((1 - t^2) P'(t)^2) = 2 sin^2(theta) / (n (D_n - u P_n))^2.
-__global__ void gl_kernel(int N, double* t_out, double* w_out, double* s_out) {
+__global__ void gl_kernel(int N, double* t_out, double* w_out, double* s_out, float* tf, float* sf) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = N + 1;
   if (k >= (n + 1) / 2) return;
@@ -63,14 +63,18 @@ __global__ void gl_kernel(int N, double* t_out, double* w_out, double* s_out) {
   t_out[k] = ct;
   w_out[k] = w;
   s_out[k] = st;
+  tf[k] = (float)ct;
+  sf[k] = (float)st;
   if (!middle) {
     t_out[N - k] = -ct;
     w_out[N - k] = w;
     s_out[N - k] = st;
+    tf[N - k] = -(float)ct;
+    sf[N - k] = (float)st;
   }
 }
 
-__global__ void phi_kernel(int L, double* cphi, double* sphi, double2* W64, float2* W32) {
+__global__ void phi_kernel(int L, double* cphi, double* sphi, double2* W64, float2* W32, float* cpf, float* spf) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= L) return;
   double s, c;
@@ -79,6 +83,8 @@ __global__ void phi_kernel(int L, double* cphi, double* sphi, double2* W64, floa
   sphi[j] = s;
   W64[j] = make_double2(c, -s);      // exp(-2 pi i j / L)
   if (W32) W32[j] = make_float2((float)c, (float)-s);
+  cpf[j] = (float)c;
+  spf[j] = (float)s;
 }
 
 // a_lm = sqrt((4l^2 - 1)/(l^2 - m^2)), b_lm = sqrt(((l-1)^2 - m^2)/(4(l-1)^2 - 1)),
@@ -133,8 +139,8 @@ __global__ void legendre_gen_kernel(int N, int hc, const double* __restrict__ t,
 
 void build_grid_tables(GridTables& g, bool want32, bool want64, cudaStream_t s, int64_t* launches) {
   const int N = g.N, L = 2 * N + 2;
-  gl_kernel<<<(N + 2) / 2 / 128 + 1, 128, 0, s>>>(N, g.t, g.w, g.s);
-  phi_kernel<<<(L + 255) / 256, 256, 0, s>>>(L, g.cphi, g.sphi, g.W64, want32 ? g.W32 : nullptr);
+  gl_kernel<<<(N + 2) / 2 / 128 + 1, 128, 0, s>>>(N, g.t, g.w, g.s, g.tf, g.sf);
+  phi_kernel<<<(L + 255) / 256, 256, 0, s>>>(L, g.cphi, g.sphi, g.W64, want32 ? g.W32 : nullptr, g.cpf, g.spf);
   rec_kernel<<<N + 1, 256, 0, s>>>(N, g.a_rec, g.b_rec);
   dim3 grid((g.hc + 63) / 64, N + 1);
   legendre_gen_kernel<<<grid, 64, 0, s>>>(N, g.hc, g.t, g.w, g.s, g.a_rec, g.b_rec, want64 ? g.A64 : nullptr,

@@ -20,15 +20,14 @@
 //             the first coefficient of the regularised problem (eq. regularized
 //             MLS problem) in closed form (Schur complement of its normal equations).
 //
-// Execution: a warp takes 32 grid nodes (heaviest first). For each node the 32
-// lanes stream its candidates (coalesced runs of the sorted points), test the
-// ball, accumulate the moments and reduce them with shuffles; the reduced
-// moments are parked in shared memory. Then the 32 lanes solve the 32 local
-// problems side by side, one per lane.
+// Execution: the gather kernel gives each grid node (heaviest first) to one
+// warp: the 32 lanes stream its candidates (coalesced runs of the sorted
+// points), test the ball, accumulate the moments and reduce-scatter them into
+// a moment buffer. The solve kernel then runs one local problem per thread.
 //
 // Precision forms: FP64 (everything in double) and MIXED (FP32 gather and
 // moments on centred, delta-scaled coordinates, FP32 solve; nodes whose FP32
-// Cholesky meets a tiny pivot are re-solved in FP64 by a second kernel).
+// Cholesky meets a tiny pivot are re-solved in FP64 from the same moments).
 #include <type_traits>
 #include "common.cuh"
 #include "kernels.h"
@@ -76,7 +75,9 @@ __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 // The local problem from its moments. mw: NM weighted moments, my: NY value
 // moments (unnormalised weights). Returns c1; also chi, tau~, the smallest
 // squared pivot and the number of dropped directions.
-template <typename S, int K>
+// BT: arithmetic of the bisection for tau (FP32 is enough when S = double
+// only serves to make the Cholesky of an ill-conditioned FP32 Gram reliable).
+template <typename S, int K, typename BT = S>
 __device__ __forceinline__ S solve_local(const S* mw, const S* my, const SolveParams& P, S& chi_out, S& tau_out,
                                          S& minpiv, int& ndrop) {
   constexpr int m = Shape<K>::m, mm = m - 1, D2 = 2 * K, D1 = K;
@@ -151,19 +152,22 @@ __device__ __forceinline__ S solve_local(const S* mw, const S* my, const SolvePa
   S tt = S(0);
   const S chiT = S(P.chiT);
   if (chi > chiT) {
-    const S rstar = S(1) - S(1) / chiT;
-    S lo = S(0), hi = r0 / (S(P.mu[1]) * rstar);
-    const S tol = sizeof(S) == 8 ? S(1e-16) : S(1e-7);
-    for (int it = 0; it < 200; ++it) {
-      const S mid = S(0.5) * (lo + hi);
-      S r = S(0);
+    BT Db[K + 1];
 #pragma unroll
-      for (int l = 1; l <= K; ++l) r += Dl[l] / (S(1) + mid * S(P.mu[l]));
+    for (int l = 1; l <= K; ++l) Db[l] = BT(Dl[l]);
+    const BT rstar = BT(1) - BT(1) / BT(P.chiT);
+    BT lo = BT(0), hi = BT(r0) / (BT(P.mu[1]) * rstar);
+    const BT tol = sizeof(BT) == 8 ? BT(1e-16) : BT(1e-7);
+    for (int it = 0; it < 200; ++it) {
+      const BT mid = BT(0.5) * (lo + hi);
+      BT r = BT(0);
+#pragma unroll
+      for (int l = 1; l <= K; ++l) r += Db[l] / (BT(1) + mid * BT(P.mu[l]));
       if (r > rstar) lo = mid;
       else hi = mid;
       if (hi - lo <= tol * hi) break;
     }
-    const S tau = S(0.5) * (lo + hi);
+    const S tau = S(BT(0.5) * (lo + hi));
     S t = (chi == inf) ? S(1) : (chi - chiT) / (S(P.chiF) - chiT);
     t = t < S(1) ? t : S(1);
     tt = smoothstep3(t) * tau;
@@ -209,53 +213,101 @@ __device__ __forceinline__ void accumulate(T (&acc)[Shape<K>::NV], T w, T u, T v
 
 constexpr int MLS_WARPS = 4;
 
+// Warp reduce-scatter of up to 64 per-lane partial sums: five exchange steps
+// halve the set each lane carries (62 shuffles instead of 5 NV), after which
+// lane l holds the totals of entries 2l and 2l+1.
+template <typename T, int NV>
+__device__ __forceinline__ void reduce_scatter64(const T (&acc)[NV], T& out0, T& out1) {
+  static_assert(NV <= 64, "at most 64 moments");
+  const int lane = threadIdx.x & 31;
+  T v[32];
+  {
+    const bool b = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const T lo = i < NV ? acc[i] : T(0);
+      const T hi = (i + 32) < NV ? acc[(i + 32) < NV ? i + 32 : 0] : T(0);
+      v[i] = (b ? hi : lo) + __shfl_xor_sync(FULL, b ? lo : hi, 16);
+    }
+  }
+#pragma unroll
+  for (int w = 16, o = 8; w >= 2; w >>= 1, o >>= 1) {
+    const bool b = lane & o;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      if (i < w) {
+        const T lo = v[i], hi = v[i + w];
+        v[i] = (b ? hi : lo) + __shfl_xor_sync(FULL, b ? lo : hi, o);
+      }
+    }
+  }
+  out0 = v[0];
+  out1 = v[1];
+}
+
+// Gather: one warp per grid node (heaviest first; the `heavy` first nodes of
+// the work order are handed out one at a time, the rest in chunks of 16). The
+// warp streams the node's candidates, accumulates the moments and writes them
+// to mom[position * NVP + i] for the solve kernel.
 template <int K, bool MIXED>
-__global__ void __launch_bounds__(MLS_WARPS * 32) mls_kernel(MlsArgs a, SolveParams P, unsigned long long* batch_ctr) {
+__global__ void __launch_bounds__(MLS_WARPS * 32) mls_gather_kernel(MlsArgs a, unsigned long long* ctr,
+                                                                    long long heavy) {
   using T = typename std::conditional<MIXED, float, double>::type;
-  constexpr int NV = Shape<K>::NV, NM = Shape<K>::NM;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 32 * NV;
+  constexpr int NV = Shape<K>::NV, NVP = (NV + 1) & ~1;
+  const int lane = threadIdx.x & 31;
   const int L = 2 * a.N + 2;
+  T* mom = reinterpret_cast<T*>(a.mom);
   for (;;) {
-    unsigned long long batch = 0;
-    if (lane == 0) batch = atomicAdd(batch_ctr, 1ull);
-    batch = __shfl_sync(FULL, batch, 0);
-    const long long first = (long long)batch * 32;
-    if (first >= a.MQ) break;
-    const int nb = (int)min(32ll, (long long)a.MQ - first);
-    for (int jb = 0; jb < nb; ++jb) {
-      const int j = (int)a.order[first + jb];
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(ctr, 1ull);
+    c = __shfl_sync(FULL, c, 0);
+    long long p0, p1;
+    if ((long long)c < heavy) {
+      p0 = (long long)c;
+      p1 = p0 + 1;
+    } else {
+      p0 = heavy + ((long long)c - heavy) * 16;
+      p1 = p0 + 16;
+    }
+    if (p0 >= a.MQ) break;
+    if (p1 > a.MQ) p1 = a.MQ;
+    for (long long pos = p0; pos < p1; ++pos) {
+      const int j = (int)a.order[pos];
       const int k = j / L, jj = j - k * L;
-      const double st = a.ring_s[k], ct = a.ring_t[k], cp = a.cphi[jj], sp = a.sphi[jj];
-      const double qx = st * cp, qy = st * sp, qz = ct;
-      const double delta = a.delta[j], rho2 = a.rho2[j];
-      // tangent frame scaled by 1/delta: e1 = d/dtheta, e2 = d/dphi
-      const double id = 1.0 / delta;
-      const T e1x = T(ct * cp * id), e1y = T(ct * sp * id), e1z = T(-st * id);
-      const T e2x = T(-sp * id), e2y = T(cp * id);
-      const T idT = T(id);
       T acc[NV];
 #pragma unroll
       for (int i = 0; i < NV; ++i) acc[i] = T(0);
-      Cap cap = make_cap(qx, qy, qz, delta);
       if (MIXED) {
-        const float qxf = (float)qx, qyf = (float)qy, qzf = (float)qz, r2f = (float)rho2;
+        // FP32 throughout: grid tables, support radius and frame in FP32
+        const float st = a.sf[k], ct = a.tf[k], cp = a.cpf[jj], sp = a.spf[jj];
+        const float qxf = st * cp, qyf = st * sp, qzf = ct;
+        const float df = a.deltaf[j], r2f = a.rho2f[j], idf = 1.f / df;
+        const float e1x = ct * cp * idf, e1y = ct * sp * idf, e1z = -st * idf;
+        const float e2x = -sp * idf, e2y = cp * idf;
+        Cap cap = make_cap_f(qxf, qyf, qzf, df);
         for_cap_candidates(a.nodes, cap, [&](bool valid, uint32_t idx) {
           if (!valid) return;
           const float4 p = a.nodes.pf[idx];
           const float dx = p.x - qxf, dy = p.y - qyf, dz = p.z - qzf;
           const float c2 = dx * dx + dy * dy + dz * dz;
           if (!(c2 < r2f)) return;
-          float w = wendland(geodesic_from_chord2(c2) * (float)idT);
+          float w = wendland(geodesic_from_chord2(c2) * idf);
           if (a.swf) w *= a.swf[idx];
           const float u = e1x * dx + e1y * dy + e1z * dz;
           const float v = e2x * dx + e2y * dy;
           accumulate<T, K>(acc, (T)w, (T)u, (T)v, (T)p.w);
         });
       } else {
+        const double st = a.ring_s[k], ct = a.ring_t[k], cp = a.cphi[jj], sp = a.sphi[jj];
+        const double qx = st * cp, qy = st * sp, qz = ct;
+        const double delta = a.delta[j], rho2 = a.rho2[j];
+        // tangent frame scaled by 1/delta: e1 = d/dtheta, e2 = d/dphi
+        const double id = 1.0 / delta;
+        const double e1x = ct * cp * id, e1y = ct * sp * id, e1z = -st * id;
+        const double e2x = -sp * id, e2y = cp * id;
         const float qxf = (float)qx, qyf = (float)qy, qzf = (float)qz;
         const float hi_f = (float)(rho2 + 1e-6 * sqrt(rho2) + 1e-6 * rho2 + 1e-13);
+        Cap cap = make_cap_f(qxf, qyf, qzf, a.deltaf[j]);
         for_cap_candidates(a.nodes, cap, [&](bool valid, uint32_t idx) {
           if (!valid) return;
           const float4 p = a.nodes.pf[idx];
@@ -267,76 +319,86 @@ __global__ void __launch_bounds__(MLS_WARPS * 32) mls_kernel(MlsArgs a, SolvePar
           const double dx = X - qx, dy = Y - qy, dz = Z - qz;
           double w = wendland(geodesic_from_chord2(c2) * id);
           if (a.sw) w *= a.sw[idx];
-          const double u = (double)e1x * dx + (double)e1y * dy + (double)e1z * dz;
-          const double v = (double)e2x * dx + (double)e2y * dy;
+          const double u = e1x * dx + e1y * dy + e1z * dz;
+          const double v = e2x * dx + e2y * dy;
           accumulate<T, K>(acc, (T)w, (T)u, (T)v, (T)a.sy[idx]);
         });
       }
-#pragma unroll
-      for (int i = 0; i < NV; ++i) acc[i] = warp_sum(acc[i]);
-      if (lane == jb) {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) sm[lane * NV + i] = acc[i];
-      }
+      T o0, o1;
+      reduce_scatter64<T, NV>(acc, o0, o1);
+      T* dst = mom + pos * NVP;
+      if (2 * lane < NV) dst[2 * lane] = o0;
+      if (2 * lane + 1 < NV) dst[2 * lane + 1] = o1;
     }
-    __syncwarp();
-    // one local problem per lane
-    const bool act = lane < nb;
-    const int j = act ? (int)a.order[first + lane] : 0;
-    T mom[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) mom[i] = act ? sm[lane * NV + i] : (i == 0 ? T(1) : T(0));
-    T chi, tau, minpiv;
-    int ndrop;
-    T c1 = solve_local<T, K>(mom, mom + NM, P, chi, tau, minpiv, ndrop);
-    bool redo = false;
-    if (MIXED) redo = act && (ndrop > 0 || !(minpiv >= T(a.fp64_pivot)) || !isfinite(c1));
-    if (act && !redo) {
-      a.fgrid[j] = (double)c1;
-      a.chi[j] = (double)chi;
-      a.tau[j] = (double)tau;
-    }
-    if (redo) {
-      unsigned long long pos = atomicAdd(&a.st->cnt[C_REDO_LIST], 1ull);
-      a.redo_node[pos] = (uint32_t)j;
-#pragma unroll
-      for (int i = 0; i < NV; ++i) a.redo_mom[pos * NV + i] = (float)mom[i];
-    }
-    unsigned long long nreg = __popc(__ballot_sync(FULL, act && !redo && tau > T(0)));
-    unsigned long long nd = warp_sum((unsigned long long)((act && !redo) ? ndrop : 0));
-    if (lane == 0) {
-      if (nreg) atomicAdd(&a.st->cnt[C_REG], nreg);
-      if (nd) atomicAdd(&a.st->cnt[C_DROP], nd);
-    }
-    __syncwarp();
   }
 }
 
-// MIXED: FP64 re-solve of the nodes whose FP32 Cholesky met a tiny pivot.
+// Solve: one thread per grid node. MIXED solves in FP32; a node whose FP32
+// Cholesky meets a tiny pivot is appended to a list and re-solved in FP64 by
+// redo_kernel, so the FP64 work runs on full warps instead of diverging here.
+template <int K, bool MIXED>
+__global__ void __launch_bounds__(128) mls_solve_kernel(MlsArgs a, SolveParams P) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  constexpr int NV = Shape<K>::NV, NM = Shape<K>::NM, NVP = (NV + 1) & ~1;
+  const long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool act = pos < a.MQ;
+  const T* src = reinterpret_cast<const T*>(a.mom) + (act ? pos : 0) * NVP;
+  T mom[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) mom[i] = act ? src[i] : (i == 0 ? T(1) : T(0));
+  T chi, tau, minpiv;
+  int ndrop;
+  const T c1 = solve_local<T, K>(mom, mom + NM, P, chi, tau, minpiv, ndrop);
+  const bool redo = MIXED && act && (ndrop > 0 || !(minpiv >= T(a.fp64_pivot)) || !isfinite(c1));
+  if (act && !redo) {
+    const int j = (int)a.order[pos];
+    a.fgrid[j] = (double)c1;
+    a.chi[j] = (double)chi;
+    a.tau[j] = (double)tau;
+  }
+  const unsigned rb = __ballot_sync(FULL, redo);
+  if (rb) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&a.st->cnt[C_REDO_LIST], (unsigned long long)__popc(rb));
+    base = __shfl_sync(FULL, base, 0);
+    if (redo) a.redo_list[base + __popc(rb & ((1u << lane) - 1u))] = (uint32_t)pos;
+  }
+  const unsigned long long nreg = __popc(__ballot_sync(FULL, act && !redo && tau > T(0)));
+  const unsigned long long nd = warp_sum((unsigned long long)((act && !redo) ? ndrop : 0));
+  if (lane == 0) {
+    if (nreg) atomicAdd(&a.st->cnt[C_REG], nreg);
+    if (nd) atomicAdd(&a.st->cnt[C_DROP], nd);
+  }
+}
+
+// MIXED: FP64 local solves of the listed nodes from their FP32 moments.
 template <int K>
 __global__ void __launch_bounds__(128) redo_kernel(MlsArgs a, SolveParams P) {
-  constexpr int NV = Shape<K>::NV, NM = Shape<K>::NM;
+  constexpr int NV = Shape<K>::NV, NM = Shape<K>::NM, NVP = (NV + 1) & ~1;
   const int lane = threadIdx.x & 31;
   const long long total = (long long)a.st->cnt[C_REDO_LIST];
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < total; e0 += stride) {
     const long long e = e0 + lane;
     const bool act = e < total;
+    const long long pos = act ? (long long)a.redo_list[e] : 0;
+    const float* src = reinterpret_cast<const float*>(a.mom) + pos * NVP;
     double mom[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) mom[i] = act ? (double)a.redo_mom[e * NV + i] : (i == 0 ? 1.0 : 0.0);
+    for (int i = 0; i < NV; ++i) mom[i] = act ? (double)src[i] : (i == 0 ? 1.0 : 0.0);
     double chi, tau, minpiv;
     int ndrop;
-    double c1 = solve_local<double, K>(mom, mom + NM, P, chi, tau, minpiv, ndrop);
+    const double c1 = solve_local<double, K, float>(mom, mom + NM, P, chi, tau, minpiv, ndrop);
     if (act) {
-      const int j = (int)a.redo_node[e];
+      const int j = (int)a.order[pos];
       a.fgrid[j] = c1;
       a.chi[j] = chi;
       a.tau[j] = tau;
     }
-    unsigned long long nreg = __popc(__ballot_sync(FULL, act && tau > 0.0));
-    unsigned long long nd = warp_sum((unsigned long long)(act ? ndrop : 0));
-    unsigned long long nr = __popc(__ballot_sync(FULL, act));
+    const unsigned long long nreg = __popc(__ballot_sync(FULL, act && tau > 0.0));
+    const unsigned long long nd = warp_sum((unsigned long long)(act ? ndrop : 0));
+    const unsigned long long nr = __popc(__ballot_sync(FULL, act));
     if (lane == 0) {
       atomicAdd(&a.st->cnt[C_REG], nreg);
       atomicAdd(&a.st->cnt[C_DROP], nd);
@@ -348,21 +410,15 @@ __global__ void __launch_bounds__(128) redo_kernel(MlsArgs a, SolveParams P) {
 template <int K, bool MIXED>
 static void launch_mls(const MlsArgs& a, const SolveParams& P, unsigned long long* ctr, cudaStream_t s,
                        int64_t* launches) {
-  using T = typename std::conditional<MIXED, float, double>::type;
-  const size_t smem = (size_t)MLS_WARPS * 32 * Shape<K>::NV * sizeof(T);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(mls_kernel<K, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_set = true;
-  }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mls_kernel<K, MIXED>, MLS_WARPS * 32, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mls_gather_kernel<K, MIXED>, MLS_WARPS * 32, 0);
   if (per_sm < 1) per_sm = 1;
-  const int blocks = per_sm * a.num_sms;
-  mls_kernel<K, MIXED><<<blocks, MLS_WARPS * 32, smem, s>>>(a, P, ctr);
-  ++*launches;
+  const long long heavy = a.MQ < 4096 ? a.MQ : (a.MQ / 8 > 4096 ? a.MQ / 8 : 4096);
+  mls_gather_kernel<K, MIXED><<<per_sm * a.num_sms, MLS_WARPS * 32, 0, s>>>(a, ctr, heavy);
+  mls_solve_kernel<K, MIXED><<<(a.MQ + 127) / 128, 128, 0, s>>>(a, P);
+  *launches += 2;
   if (MIXED) {
-    redo_kernel<K><<<a.num_sms * 4, 128, 0, s>>>(a, P);
+    redo_kernel<K><<<a.num_sms * 8, 128, 0, s>>>(a, P);
     ++*launches;
   }
 }
@@ -385,6 +441,11 @@ void run_mls(const MlsArgs& a, bool mixed, cudaStream_t s, int64_t* launches) {
     case 9: launch_mls<4, true>(a, P, ctr, s, launches); break;
     default: break;
   }
+}
+
+int mls_moment_slots(int K) {
+  const int nv = dim_tan(2 * K) + dim_tan(K);
+  return (nv + 1) & ~1;
 }
 
 }  // namespace hamls

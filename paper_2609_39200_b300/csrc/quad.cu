@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) legendre_kernel(int N, int hc, const T* _
 
 template <typename T>
 static void launch_quad(const QuadArgs& a, const typename C2<T>::t* W, const T* A, cudaStream_t s,
-                        int64_t* launches) {
+                        int64_t* launches, int part) {
   using cT = typename C2<T>::t;
   const int N = a.g->N, L = 2 * N + 2, hc = a.g->hc;
   const size_t smem_fft = 2 * (size_t)L * sizeof(cT);
@@ -152,16 +152,21 @@ static void launch_quad(const QuadArgs& a, const typename C2<T>::t* W, const T* 
     cudaFuncSetAttribute(legendre_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  ring_fft_kernel<T><<<(N + 2) / 2, 256, smem_fft, s>>>(a.fgrid, N, a, W, reinterpret_cast<cT*>(a.F));
-  legendre_kernel<T><<<N + 1, 256, smem_leg, s>>>(N, hc, A, reinterpret_cast<const cT*>(a.F), a.coeffs);
-  *launches += 2;
+  if (part & 1) {
+    ring_fft_kernel<T><<<(N + 2) / 2, 256, smem_fft, s>>>(a.fgrid, N, a, W, reinterpret_cast<cT*>(a.F));
+    ++*launches;
+  }
+  if (part & 2) {
+    legendre_kernel<T><<<N + 1, 256, smem_leg, s>>>(N, hc, A, reinterpret_cast<const cT*>(a.F), a.coeffs);
+    ++*launches;
+  }
 }
 
-void run_quadrature(const QuadArgs& a, bool mixed, cudaStream_t s, int64_t* launches) {
+void run_quadrature(const QuadArgs& a, bool mixed, cudaStream_t s, int64_t* launches, int part) {
   if (mixed)
-    launch_quad<float>(a, a.g->W32, a.g->A32, s, launches);
+    launch_quad<float>(a, a.g->W32, a.g->A32, s, launches, part);
   else
-    launch_quad<double>(a, a.g->W64, a.g->A64, s, launches);
+    launch_quad<double>(a, a.g->W64, a.g->A64, s, launches, part);
 }
 
 }  // namespace hamls
