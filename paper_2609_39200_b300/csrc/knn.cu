@@ -135,35 +135,19 @@ __device__ double knn_nth_exact(const Cells& g, double qx, double qy, double qz,
 // query (see c2_margin), evaluated in FP32 with slack.
 __device__ __forceinline__ float c2_margin_f(float c2) { return 1.05e-6f * sqrtf(c2) + 1.05e-6f * c2 + 1e-13f; }
 
-constexpr int KNN_EXTRA = 8;                       // FP32 keys kept beyond the n-th
-constexpr int KNN_LIST = KNN_MAX + KNN_EXTRA;      // warp list capacity
-constexpr int KNN_SCRATCH = KNN_LIST * 8;          // bytes of warp scratch knn_nth needs
+constexpr int KL_MAX = 16;                             // FP32 chords a lane keeps (n > 48)
+constexpr int KNN_SCRATCH = KNN_MAX * 8 + 32 * 4;      // warp scratch: exact-path list, uncertain ids
 
-// n-th smallest exact squared chord from q to the points of g, found in FP32:
-// the scan keeps the H = n + 8 smallest FP32 chords (with indices) in a sorted
-// warp list; then only the few candidates whose FP32 chord lies within twice
-// the FP32 error bound m of the n-th FP32 value T are measured exactly. With
-// A = #{FP32 chord < T - 2m}, those A are certainly among the n nearest and
-// the answer is the (n - A)-th smallest exact chord of the uncertain ones.
-// It needs every uncertain candidate in the list (its last key > T + 2m, or
-// fewer than H candidates): otherwise, or with more than 32 uncertain ones,
-// the exact FP64 search runs instead.
-__device__ double knn_nth(const Cells& g, double qx, double qy, double qz, int n, unsigned char* scratch,
-                          double r0, bool* failed, unsigned long long* exact_fb = nullptr) {
-  const int lane = threadIdx.x & 31;
-  const float qxf = (float)qx, qyf = (float)qy, qzf = (float)qz;
-  const float INF_F = __int_as_float(0x7f800000);
-  const int H = n + KNN_EXTRA;
-  float* lkey = reinterpret_cast<float*>(scratch);
-  uint32_t* lidx = reinterpret_cast<uint32_t*>(lkey + KNN_LIST);
+// Phase 1 of a search without a known radius: a radius whose candidate
+// enumeration (counted from the run table alone) holds a few times n points.
+__device__ float knn_initial_radius(const Cells& g, float qxf, float qyf, float qzf, int n, float r0) {
   const float PI_F = 3.14159265f;
-  // phase 1: a radius whose enumeration holds a few times n candidates
-  float r = fminf(fmaxf((float)r0, 1e-7f), PI_F), rlo = 0.f, rhi = PI_F;
+  float r = fminf(fmaxf(r0, 1e-7f), PI_F), rlo = 0.f, rhi = PI_F;
   bool have_lo = false, have_hi = false;
   const uint32_t lowT = (uint32_t)n + (uint32_t)n / 4 + 4u, highT = 16u * (uint32_t)n + 64u;
   for (int it = 0; it < 80; ++it) {
     Cap c = make_cap_f(qxf, qyf, qzf, r);
-    uint32_t bc = cap_box_count(g, c);
+    const uint32_t bc = cap_box_count(g, c);
     if (bc < lowT) {
       if (r >= PI_F) break;
       rlo = r;
@@ -187,346 +171,221 @@ __device__ double knn_nth(const Cells& g, double qx, double qy, double qz, int n
       r = 0.5f * r;
     }
   }
-  // phase 2
-  for (int it = 0; it < 64; ++it) {
-    for (int i = lane; i < H; i += 32) {
-      lkey[i] = INF_F;
-      lidx[i] = 0xFFFFFFFFu;
-    }
-    __syncwarp();
-    float thr = INF_F;
-    Cap c = make_cap_f(qxf, qyf, qzf, r);
-    for_cap_candidates(g, c, [&](bool valid, uint32_t idx) {
-      float c2f = INF_F;
-      if (valid) {
-        const float4 p = g.pf[idx];
-        const float dx = p.x - qxf, dy = p.y - qyf, dz = p.z - qzf;
-        c2f = dx * dx + dy * dy + dz * dz;
-      }
-      unsigned ball = __ballot_sync(FULL, valid && c2f < thr);
-      while (ball) {
-        const int src = __ffs(ball) - 1;
-        ball &= ball - 1;
-        const float v = __shfl_sync(FULL, c2f, src);
-        const uint32_t vi = __shfl_sync(FULL, idx, src);
-        if (v < lkey[H - 1]) {
-          int pos = 0;
-          for (int k0 = 0; k0 < H; k0 += 32) {
-            const int i = k0 + lane;
-            pos += __popc(__ballot_sync(FULL, i < H && lkey[i] <= v));
-          }
-          float pk[(KNN_LIST + 31) / 32];
-          uint32_t pi[(KNN_LIST + 31) / 32];
+  return r;
+}
+
+__device__ __forceinline__ float geodesic_f(float c2) { return 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2))); }
+
+// One scan of the cap of radius r. Every lane keeps, in registers, the KL
+// smallest FP32 squared chords among the candidates it is dealt (sorted,
+// with indices) - no warp-serialised list. The n-th smallest key T over the
+// warp is bracketed, tl < T <= th, by a bisection on values that stops once
+// th - tl is within the FP32 error bound m or (tl, th] holds one key. Then
+// keys < tl - 2m are certainly among the n nearest (A of them), keys above
+// th + 2m certainly not, and the answer is the (n - A)-th smallest exact FP64
+// chord among the keys in [tl - 2m, th + 2m].
+// Returns 0 with the exact n-th chord in nth, 1 when the cap was too small
+// (r_next to retry), 2 when a lane's list may have dropped a needed key or
+// too many keys are uncertain (the caller runs the exact search).
+template <int KL>
+__device__ int knn_select(const Cells& g, double qx, double qy, double qz, float r, int n, uint32_t* ustage,
+                          double& nth, float& r_next) {
+  const int lane = threadIdx.x & 31;
+  const float PI_F = 3.14159265f;
+  const float INF_F = __int_as_float(0x7f800000);
+  const float qxf = (float)qx, qyf = (float)qy, qzf = (float)qz;
+  float key[KL];
+  uint32_t kid[KL];
 #pragma unroll
-          for (int kk = 0; kk < (KNN_LIST + 31) / 32; ++kk) {
-            const int i = kk * 32 + lane;
-            pk[kk] = (i >= 1 && i < H) ? lkey[i - 1] : 0.f;
-            pi[kk] = (i >= 1 && i < H) ? lidx[i - 1] : 0u;
-          }
-          __syncwarp();
+  for (int s2 = 0; s2 < KL; ++s2) {
+    key[s2] = INF_F;
+    kid[s2] = 0xFFFFFFFFu;
+  }
+  Cap c = make_cap_f(qxf, qyf, qzf, r);
+  for_cap_candidates<true>(g, c, [&](bool valid, uint32_t idx) {
+    if (!valid) return;
+    const float4 p = g.pf[idx];
+    const float dx = p.x - qxf, dy = p.y - qyf, dz = p.z - qzf;
+    float x = dx * dx + dy * dy + dz * dz;
+    if (x < key[KL - 1]) {
+      uint32_t xi = idx;
 #pragma unroll
-          for (int kk = 0; kk < (KNN_LIST + 31) / 32; ++kk) {
-            const int i = kk * 32 + lane;
-            if (i > pos && i < H) {
-              lkey[i] = pk[kk];
-              lidx[i] = pi[kk];
-            }
-          }
-          if (lane == (pos & 31) && pos < H) {
-            lkey[pos] = v;
-            lidx[pos] = vi;
-          }
-          __syncwarp();
+      for (int s2 = 0; s2 < KL; ++s2) {
+        if (x < key[s2]) {
+          const float t = key[s2];
+          key[s2] = x;
+          x = t;
+          const uint32_t ti = kid[s2];
+          kid[s2] = xi;
+          xi = ti;
         }
       }
-      thr = lkey[H - 1];
-    });
-    __syncwarp();
-    const float T = lkey[n - 1];
-    if (!(T < INF_F)) {                               // fewer than n candidates so far
-      if (r >= PI_F) {
-        *failed = true;
-        return __longlong_as_double(0x7ff0000000000000ll);
-      }
-      r = fminf(PI_F, fmaxf(2.f * r, 0.25f * (float)r0));
-      continue;
     }
-    const float m = c2_margin_f(T);
-    const float last = lkey[H - 1];
-    int A = 0, u0 = H, u1 = 0;
-    for (int k0 = 0; k0 < H; k0 += 32) {
-      const int i = k0 + lane;
-      const float kv = i < H ? lkey[i] : INF_F;
-      A += __popc(__ballot_sync(FULL, i < H && kv < T - 2.f * m));
-      const unsigned inu = __ballot_sync(FULL, i < H && kv >= T - 2.f * m && kv <= T + 2.f * m);
-      if (inu) {
-        u0 = min(u0, k0 + __ffs(inu) - 1);
-        u1 = max(u1, k0 + 32 - __clz(inu));
-      }
+  });
+  int fin = 0;
+#pragma unroll
+  for (int s2 = 0; s2 < KL; ++s2) fin += key[s2] < INF_F ? 1 : 0;
+  if (warp_sum(fin) < n) {                          // fewer than n points in the cap
+    if (__any_sync(FULL, key[KL - 1] < INF_F)) return 2;  // unless a lane list overflowed
+    r_next = fminf(PI_F, 2.f * r);
+    return 1;
+  }
+  // Isolate the n-th smallest key T in a window [tl, th] with count(<= tl) < n
+  // <= count(<= th) by bisection on values, stopping once the window is
+  // narrower than the FP32 error bound (or holds the n-th key alone); the
+  // uncertain set below is then taken around that window.
+  float tl = __uint_as_float(0x7f7fffffu), th = 0.f;
+#pragma unroll
+  for (int s2 = 0; s2 < KL; ++s2)
+    if (key[s2] < INF_F) th = fmaxf(th, key[s2]);
+  tl = fminf(tl, key[0]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tl = fminf(tl, __shfl_xor_sync(FULL, tl, o));
+    th = fmaxf(th, __shfl_xor_sync(FULL, th, o));
+  }
+  tl = tl * (1.f - 1e-6f) - 1e-30f;                 // count(<= tl) = 0 < n; count(<= th) >= n
+  for (int it = 0; it < 40; ++it) {
+    if (th - tl <= c2_margin_f(th)) break;
+    const float mid = 0.5f * (tl + th);
+    int cnt = 0;
+#pragma unroll
+    for (int s2 = 0; s2 < KL; ++s2) cnt += key[s2] <= mid ? 1 : 0;
+    const int c = warp_sum(cnt);
+    if (c >= n) th = mid;
+    else tl = mid;
+    // stop when (tl, th] holds exactly one key value (the n-th)
+    if (c == n || c == n - 1) {
+      int inwin = 0;
+#pragma unroll
+      for (int s2 = 0; s2 < KL; ++s2) inwin += (key[s2] > tl && key[s2] <= th) ? 1 : 0;
+      if (warp_sum(inwin) <= 1) break;
     }
-    const int nu = u1 - u0;
+  }
+  const float m = c2_margin_f(th);
+  const float tlo = tl - 2.f * m, thi = th + 2.f * m;
+  // a full lane list dropped keys >= its last one: they must lie above thi
+  if (__any_sync(FULL, key[KL - 1] <= thi)) return 2;
+  int A = 0, mine = 0;
+#pragma unroll
+  for (int s2 = 0; s2 < KL; ++s2) {
+    A += key[s2] < tlo ? 1 : 0;
+    mine += (key[s2] >= tlo && key[s2] <= thi) ? 1 : 0;
+  }
+  A = warp_sum(A);
+  int incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int nu = __shfl_sync(FULL, incl, 31);
+  if (nu > 32 || n - A < 1 || nu < n - A) return 2;
+  int off = incl - mine;
+#pragma unroll
+  for (int s2 = 0; s2 < KL; ++s2)
+    if (key[s2] >= tlo && key[s2] <= thi) ustage[off++] = kid[s2];
+  __syncwarp();
+  double e = __longlong_as_double(0x7ff0000000000000ll);
+  if (lane < nu) {
+    const uint32_t id = ustage[lane];
+    e = chord2_exact(g.px[id], g.py[id], g.pz[id], qx, qy, qz);
+  }
+  int rank = 0;
+  for (int s2 = 0; s2 < nu; ++s2) {
+    const double o = __shfl_sync(FULL, e, s2);
+    rank += (o < e || (o == e && s2 < lane)) ? 1 : 0;
+  }
+  const unsigned hit = __ballot_sync(FULL, lane < nu && rank == n - A - 1);
+  nth = __shfl_sync(FULL, e, __ffs(hit) - 1);
+  __syncwarp();
+  // every point within geodesic r of q was enumerated; is the n-th inside?
+  const float gn = geodesic_f((float)nth);
+  if (gn * (1.f + 2e-6f) <= r || r >= PI_F) return 0;
+  r_next = fminf(PI_F, fmaxf(1.25f * r, gn * (1.f + 1e-5f) + 1e-6f));
+  return 1;
+}
+
+// n-th smallest exact squared chord from q to the points of g (+inf and
+// *failed when there are fewer than n points). r_hint > 0: a radius known to
+// hold at least n points (then one scan suffices); otherwise phase 1 finds one.
+// KL: length of the per-lane lists, 12 for n <= 48, else 16.
+template <int KL>
+__device__ double knn_nth(const Cells& g, double qx, double qy, double qz, int n, unsigned char* scratch,
+                          double r0, bool* failed, unsigned long long* exact_fb = nullptr, float r_hint = -1.f) {
+  const float qxf = (float)qx, qyf = (float)qy, qzf = (float)qz;
+  float r = r_hint > 0.f ? fminf(r_hint, 3.14159265f) : knn_initial_radius(g, qxf, qyf, qzf, n, (float)r0);
+  uint32_t* ustage = reinterpret_cast<uint32_t*>(scratch + KNN_MAX * 8);
+  for (int it = 0; it < 64; ++it) {
     double nth;
-    if (!(last > T + 2.f * m || last == INF_F) || nu > 32 || nu < n - A || n - A < 1) {
-      if (exact_fb && lane == 0) atomicAdd(exact_fb, 1ull);
+    float rn = r;
+    const int rc = knn_select<KL>(g, qx, qy, qz, r, n, ustage, nth, rn);
+    if (rc == 0) return nth;
+    if (rc == 2) {
+      if (exact_fb && (threadIdx.x & 31) == 0) atomicAdd(exact_fb, 1ull);
       return knn_nth_exact(g, qx, qy, qz, n, reinterpret_cast<double*>(scratch), r0, failed);
     }
-    {
-      double e = __longlong_as_double(0x7ff0000000000000ll);
-      if (lane < nu) {
-        const uint32_t id = lidx[u0 + lane];
-        e = chord2_exact(g.px[id], g.py[id], g.pz[id], qx, qy, qz);
-      }
-      // rank of this lane's exact chord among the uncertain ones (ties by lane)
-      int rank = 0;
-      for (int s2 = 0; s2 < nu; ++s2) {
-        const double o = __shfl_sync(FULL, e, s2);
-        rank += (o < e || (o == e && s2 < lane)) ? 1 : 0;
-      }
-      const unsigned hit = __ballot_sync(FULL, lane < nu && rank == n - A - 1);
-      nth = __shfl_sync(FULL, e, __ffs(hit) - 1);
-    }
-    const double sr = sin(0.5 * (double)r);
-    const double rho2 = 4.0 * sr * sr;
-    if (nth < rho2 || r >= PI_F) return nth;
-    r = fminf(PI_F, fmaxf(1.25f * r, 2.f * asinf(fminf(1.f, 0.5f * sqrtf((float)nth))) * (1.f + 1e-5f) + 1e-6f));
+    if (r >= 3.14159265f) break;
+    r = rn;
   }
   *failed = true;
   return __longlong_as_double(0x7ff0000000000000ll);
 }
 
-// d_n at the auxiliary points, a tile of 32 neighbouring points per warp (32
-// consecutive points of an ordering by latitude bands about as tall as the
-// tile is wide, then longitude). The exact d_n of the representative r (the
-// tile point nearest the tile's centroid) bounds every other: d_n(a) <=
-// d_n(r) + d(a, r) (d_n is 1-Lipschitz), so all n nearest nodes of every tile
-// point lie within R = d_n(r) + 2 max_a d(a, r) of r. The warp streams the
-// candidates of that cap once through shared memory; each lane keeps a
-// max-heap of the H = n + 8 smallest FP32 chords from its own point. Heap
-// updates are buffered per lane and applied once per 32 staged candidates, so
-// the warp does not diverge on every insertion. The exact n-th chord then
-// follows as in knn_nth, with FP64 only for the uncertain few.
-constexpr int TK_WARPS = 2;
-constexpr int TK_PEND = 16;
+// d_n at the auxiliary points. A warp walks chunks of 32 consecutive points of
+// a spatially coherent order (coarse latitude bands, then longitude; chunks
+// handed out dynamically). Each search starts from the previous point's exact
+// d_n plus the distance between the two points: d_n is 1-Lipschitz, so that
+// cap holds at least n nodes and one scan suffices. The 32 exact chords of a
+// chunk become geodesic distances together (one FP64 asin per lane).
+constexpr int AK_WARPS = 4;
+constexpr int AK_CHUNK = 32;
 
-__host__ __device__ __forceinline__ size_t tile_warp_bytes(int n) {
-  // heap keys + indices, pending keys + indices, knn_nth scratch, staged candidates
-  return (size_t)(n + KNN_EXTRA) * 32 * 8 + (size_t)TK_PEND * 32 * 8 + KNN_SCRATCH + 32 * 16 + 32 * 4;
-}
-
-__device__ __forceinline__ void heap_replace_root(float* hkey, uint32_t* hidx, int size, int lane, float v,
-                                                  uint32_t id) {
-  int k = 0;
-  for (;;) {
-    const int l = 2 * k + 1;
-    if (l >= size) break;
-    int mc = l;
-    float hm = hkey[l * 32 + lane];
-    if (l + 1 < size) {
-      const float hr = hkey[(l + 1) * 32 + lane];
-      if (hr > hm) {
-        mc = l + 1;
-        hm = hr;
-      }
-    }
-    if (!(hm > v)) break;
-    hkey[k * 32 + lane] = hm;
-    hidx[k * 32 + lane] = hidx[mc * 32 + lane];
-    k = mc;
-  }
-  hkey[k * 32 + lane] = v;
-  hidx[k * 32 + lane] = id;
-}
-
-__global__ void __launch_bounds__(TK_WARPS * 32) aux_knn_tile_kernel(Cells nodes, Cells aux,
-                                                                     const uint32_t* __restrict__ tile_order,
-                                                                     int n, double r0, double* __restrict__ dn_sorted,
-                                                                     float* __restrict__ dn_f, DevStatus* st,
-                                                                     unsigned long long* ctr) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+template <int KL>
+__global__ void __launch_bounds__(AK_WARPS * 32) aux_knn_kernel(Cells nodes, Cells aux,
+                                                                const uint32_t* __restrict__ order, int n, double r0,
+                                                                double* __restrict__ dn_sorted,
+                                                                float* __restrict__ dn_f, DevStatus* st,
+                                                                unsigned long long* ctr) {
+  __shared__ __align__(16) unsigned char scr[AK_WARPS][KNN_SCRATCH];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int H = n + KNN_EXTRA;
-  unsigned char* base = smem_raw + warp * tile_warp_bytes(n);
-  float* hkey = reinterpret_cast<float*>(base);                      // [H][32]
-  uint32_t* hidx = reinterpret_cast<uint32_t*>(hkey + H * 32);       // [H][32]
-  float* pkey = reinterpret_cast<float*>(hidx + H * 32);             // [TK_PEND][32]
-  uint32_t* pidx = reinterpret_cast<uint32_t*>(pkey + TK_PEND * 32);  // [TK_PEND][32]
-  unsigned char* kscr = reinterpret_cast<unsigned char*>(pidx + TK_PEND * 32);
-  float4* sf = reinterpret_cast<float4*>(kscr + KNN_SCRATCH);        // [32]
-  uint32_t* si = reinterpret_cast<uint32_t*>(sf + 32);                // [32]
-  const float INF_F = __int_as_float(0x7f800000);
   for (;;) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(ctr, 1ull);
     t = __shfl_sync(FULL, t, 0);
-    const long long first = (long long)t * 32;
+    const long long first = (long long)t * AK_CHUNK;
     if (first >= aux.n) break;
-    const int cnt = (int)min(32ll, (long long)aux.n - first);
-    const bool act = lane < cnt;
-    const uint32_t fi = tile_order[first + (act ? lane : 0)];
-    const double ax = aux.px[fi], ay = aux.py[fi], az = aux.pz[fi];
-    const float axf = (float)ax, ayf = (float)ay, azf = (float)az;
-    // representative: the tile point nearest the centroid
-    const float cx = warp_sum(act ? axf : 0.f), cy = warp_sum(act ? ayf : 0.f), cz = warp_sum(act ? azf : 0.f);
-    float dc = act ? (axf - cx / cnt) * (axf - cx / cnt) + (ayf - cy / cnt) * (ayf - cy / cnt) +
-                         (azf - cz / cnt) * (azf - cz / cnt)
-                   : INF_F;
-    int rl = lane;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float od = __shfl_xor_sync(FULL, dc, o);
-      const int ol = __shfl_xor_sync(FULL, rl, o);
-      if (od < dc || (od == dc && ol < rl)) {
-        dc = od;
-        rl = ol;
-      }
-    }
-    const double rx = __shfl_sync(FULL, ax, rl), ry = __shfl_sync(FULL, ay, rl), rz = __shfl_sync(FULL, az, rl);
-    const float rxf = (float)rx, ryf = (float)ry, rzf = (float)rz;
-    // spread: an upper bound of max_a d(a, r) in FP32
-    float sp = 0.f;
-    if (act) {
-      const float dx = axf - rxf, dy = ayf - ryf, dz = azf - rzf;
-      sp = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(dx * dx + dy * dy + dz * dz)));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sp = fmaxf(sp, __shfl_xor_sync(FULL, sp, o));
+    const int cnt = (int)min((long long)AK_CHUNK, (long long)aux.n - first);
+    float prev = -1.f, pxf = 0.f, pyf = 0.f, pzf = 0.f;
+    double mine = 0.0;
     bool failed = false;
-    const double c2r = knn_nth(nodes, rx, ry, rz, n, kscr, r0, &failed, &st->cnt[C_KNN_EXACT_FB]);
-    const float dr = 2.f * asinf(fminf(1.f, 0.5f * sqrtf((float)c2r)));
-    const float R = fminf((dr + 2.f * sp) * (1.f + 1e-5f) + 1e-6f, 3.14159265f);
-    for (int k = 0; k < H; ++k) {
-      hkey[k * 32 + lane] = INF_F;
-      hidx[k * 32 + lane] = 0xFFFFFFFFu;
-    }
-    float root = INF_F;
-    int pc = 0;
-    unsigned long long ncand = 0, nins = 0;
-    __syncwarp();
-    Cap c = make_cap_f(rxf, ryf, rzf, R);
-    for_cap_candidates<true>(nodes, c, [&](bool valid, uint32_t idx) {
-      if (valid) {
-        sf[lane] = nodes.pf[idx];
-        si[lane] = idx;
+    for (int k = 0; k < cnt; ++k) {
+      const uint32_t fi = order[first + k];
+      const double ax = aux.px[fi], ay = aux.py[fi], az = aux.pz[fi];
+      const float axf = (float)ax, ayf = (float)ay, azf = (float)az;
+      float hint = -1.f;
+      if (prev >= 0.f) {
+        const float dx = axf - pxf, dy = ayf - pyf, dz = azf - pzf;
+        hint = (prev + geodesic_f(dx * dx + dy * dy + dz * dz)) * (1.f + 1e-5f) + 2e-6f;
       }
-      const int nv = __popc(__ballot_sync(FULL, valid));
-      ncand += nv;
-      __syncwarp();
-      for (int cc = 0; cc < nv; ++cc) {
-        const float4 p = sf[cc];
-        const float dx = p.x - axf, dy = p.y - ayf, dz = p.z - azf;
-        const float c2f = dx * dx + dy * dy + dz * dz;
-        if (act && c2f < root) {
-          ++nins;
-          if (pc < TK_PEND) {
-            pkey[pc * 32 + lane] = c2f;
-            pidx[pc * 32 + lane] = si[cc];
-            ++pc;
-          } else {
-            heap_replace_root(hkey, hidx, H, lane, c2f, si[cc]);
-            root = hkey[lane];
-          }
-        }
-      }
-      __syncwarp();
-      // apply the buffered insertions
-      while (__any_sync(FULL, pc > 0)) {
-        if (pc > 0) {
-          --pc;
-          const float v = pkey[pc * 32 + lane];
-          if (v < root) {
-            heap_replace_root(hkey, hidx, H, lane, v, pidx[pc * 32 + lane]);
-            root = hkey[lane];
-          }
-        }
-      }
-    });
-    // exact n-th: pop the KNN_EXTRA largest (heap sort tail), then resolve the
-    // entries within 2m of the n-th FP32 value T with FP64 chords
-    const float rootH = root;
-    int size = H;
-    for (int pp = 0; pp < KNN_EXTRA; ++pp) {
-      const float top = hkey[lane];
-      const uint32_t tid = hidx[lane];
-      --size;
-      const float lv = hkey[size * 32 + lane];
-      const uint32_t li = hidx[size * 32 + lane];
-      heap_replace_root(hkey, hidx, size, lane, lv, li);
-      hkey[size * 32 + lane] = top;
-      hidx[size * 32 + lane] = tid;
+      const double c2 = knn_nth<KL>(nodes, ax, ay, az, n, scr[warp], r0, &failed, &st->cnt[C_KNN_EXACT_FB], hint);
+      prev = (c2 < 1e300) ? geodesic_f((float)c2) : -1.f;
+      pxf = axf;
+      pyf = ayf;
+      pzf = azf;
+      if (lane == k) mine = c2;
     }
-    const float T = hkey[lane];                       // n-th smallest FP32 chord
-    const float m = c2_margin_f(T);
-    int A = 0, nu = 0;
-    double ue[8];
-#pragma unroll
-    for (int s2 = 0; s2 < 8; ++s2) ue[s2] = 0.0;
-    bool ok = act && T < INF_F && (rootH > T + 2.f * m || rootH == INF_F);
-    if (ok) {
-      for (int k = 0; k < H; ++k) {
-        const float kv = hkey[k * 32 + lane];
-        if (kv < T - 2.f * m) {
-          ++A;
-        } else if (kv <= T + 2.f * m) {
-          if (nu >= 8) {
-            ok = false;
-            break;
-          }
-          const uint32_t id = hidx[k * 32 + lane];
-          double x = chord2_exact(nodes.px[id], nodes.py[id], nodes.pz[id], ax, ay, az);
-#pragma unroll
-          for (int s2 = 0; s2 < 8; ++s2) {
-            if (s2 < nu) {
-              if (ue[s2] > x) {
-                const double tt = ue[s2];
-                ue[s2] = x;
-                x = tt;
-              }
-            } else if (s2 == nu) {
-              ue[s2] = x;
-            }
-          }
-          ++nu;
-        }
-      }
-    }
-    double res = __longlong_as_double(0x7ff0000000000000ll);
-    const int want = n - A - 1;
-    if (ok && want >= 0 && want < nu) {
-#pragma unroll
-      for (int s2 = 0; s2 < 8; ++s2)
-        if (s2 == want) res = ue[s2];
-    } else {
-      ok = false;
-    }
-    // lanes that could not conclude: exact warp search, one by one
-    unsigned redo = __ballot_sync(FULL, act && !ok);
-    nins = warp_sum(nins);
-    if (lane == 0) {
-      atomicAdd(&st->cnt[C_KNN_CAND], ncand);
-      atomicAdd(&st->cnt[C_KNN_INS], nins);
-      if (redo) atomicAdd(&st->cnt[C_KNN_LANE_FB], (unsigned long long)__popc(redo));
-    }
-    while (redo) {
-      const int src = __ffs(redo) - 1;
-      redo &= redo - 1;
-      const double qx = __shfl_sync(FULL, ax, src), qy = __shfl_sync(FULL, ay, src), qz = __shfl_sync(FULL, az, src);
-      bool f2 = false;
-      const double v = knn_nth(nodes, qx, qy, qz, n, kscr, r0, &f2, &st->cnt[C_KNN_EXACT_FB]);
-      if (lane == src) {
-        res = v;
-        failed = failed || f2;
-      }
-    }
-    if (act) {
-      if (failed || !(res < 1e300)) set_flag(st, ST_KNN);
-      const double dn = geodesic_from_chord2(res);
+    if (lane < cnt) {
+      if (failed || !(mine < 1e300)) set_flag(st, ST_KNN);
+      const uint32_t fi = order[first + lane];
+      const double dn = geodesic_from_chord2(mine);
       dn_sorted[fi] = dn;
       dn_f[fi] = (float)dn;
     }
-    __syncwarp();
   }
 }
 
+template <int KL>
 __global__ void __launch_bounds__(KNN_WARPS * 32) knn_query_kernel(Cells nodes, const double* __restrict__ q,
                                                                    int64_t nq, int n, double r0,
                                                                    double* __restrict__ out, DevStatus* st) {
@@ -535,7 +394,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_query_kernel(Cells nodes, 
   const int64_t nw = (int64_t)gridDim.x * KNN_WARPS;
   for (int64_t i = (int64_t)blockIdx.x * KNN_WARPS + warp; i < nq; i += nw) {
     bool failed = false;
-    double c2 = knn_nth(nodes, q[3 * i], q[3 * i + 1], q[3 * i + 2], n, lists[warp], r0, &failed);
+    double c2 = knn_nth<KL>(nodes, q[3 * i], q[3 * i + 1], q[3 * i + 2], n, lists[warp], r0, &failed);
     if (lane == 0) {
       if (failed) set_flag(st, ST_KNN);
       out[i] = c2;
@@ -684,7 +543,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) guard_kernel(SupportArgs a, do
     const int k = j / L, jj = j - k * L;
     const double qx = a.ring_s[k] * a.cphi[jj], qy = a.ring_s[k] * a.sphi[jj], qz = a.ring_t[k];
     bool failed = false;
-    double c2 = knn_nth(a.nodes, qx, qy, qz, a.n_target, lists[warp], r0, &failed);
+    double c2 = knn_nth<KL_MAX>(a.nodes, qx, qy, qz, a.n_target, lists[warp], r0, &failed);
     double delta = (1.0 + a.eps) * geodesic_from_chord2(c2);
     const double PI = 3.14159265358979323846;
     bool bad = failed || !(delta < 0.5 * PI);
@@ -739,19 +598,22 @@ static int grid_for(int work_warps, int warps_per_block, int cap_blocks) {
 
 static double initial_radius(int n, int M) { return 2.0 * sqrt((double)n / (double)(M > 0 ? M : 1)); }
 
-void run_aux_knn(const SupportArgs& a, cudaStream_t s, int64_t* launches) {
-  const size_t smem = tile_warp_bytes(a.n_target) * TK_WARPS;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(aux_knn_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+template <int KL>
+static void launch_aux_knn(const SupportArgs& a, cudaStream_t s) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aux_knn_tile_kernel, TK_WARPS * 32, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aux_knn_kernel<KL>, AK_WARPS * 32, 0);
   if (per_sm < 1) per_sm = 1;
-  aux_knn_tile_kernel<<<per_sm * a.num_sms, TK_WARPS * 32, smem, s>>>(
-      a.nodes, a.aux, a.tile_order, a.n_target, initial_radius(a.n_target, a.nodes.n), a.dn_aux_sorted, a.dn_aux_f,
-      a.st, &a.st->cnt[C_TILE]);
+  aux_knn_kernel<KL><<<per_sm * a.num_sms, AK_WARPS * 32, 0, s>>>(a.nodes, a.aux, a.tile_order, a.n_target,
+                                                                  initial_radius(a.n_target, a.nodes.n),
+                                                                  a.dn_aux_sorted, a.dn_aux_f, a.st,
+                                                                  &a.st->cnt[C_TILE]);
+}
+
+void run_aux_knn(const SupportArgs& a, cudaStream_t s, int64_t* launches) {
+  if (a.n_target <= 48)
+    launch_aux_knn<12>(a, s);
+  else
+    launch_aux_knn<KL_MAX>(a, s);
   ++*launches;
 }
 
@@ -778,8 +640,12 @@ void run_counts(const SupportArgs& a, cudaStream_t s, int64_t* launches) {
 void run_knn_queries(const Cells& nodes, const double* q, int64_t nq, int n, double* c2_out, DevStatus* st,
                      cudaStream_t s, int64_t* launches) {
   if (nq <= 0) return;
-  knn_query_kernel<<<grid_for((int)nq, KNN_WARPS, 148 * 16), KNN_WARPS * 32, 0, s>>>(
-      nodes, q, nq, n, initial_radius(n, nodes.n), c2_out, st);
+  const int blocks = grid_for((int)nq, KNN_WARPS, 148 * 16);
+  if (n <= 48)
+    knn_query_kernel<12><<<blocks, KNN_WARPS * 32, 0, s>>>(nodes, q, nq, n, initial_radius(n, nodes.n), c2_out, st);
+  else
+    knn_query_kernel<KL_MAX><<<blocks, KNN_WARPS * 32, 0, s>>>(nodes, q, nq, n, initial_radius(n, nodes.n), c2_out,
+                                                               st);
   ++*launches;
 }
 
