@@ -368,11 +368,12 @@ hamls_status build_static(hamls_plan_s* P, cudaStream_t s) {
   cb.perm_out = &P->aperm;
   cb.keys_out = &P->askeys;
   build_cells(cb, s, &P->launches);
-  // tile order of the auxiliary points for the k-NN: coarse latitude bands of
-  // about sqrt(32) point spacings, then longitude
+  // chain order of the auxiliary points for the k-NN: latitude bands about
+  // 1.5 point spacings high (a band is 2.8/bt to 4/bt rad high), then
+  // longitude; consecutive points then lie about one spacing apart
   const double spacing = sqrt(4.0 * M_PI / (double)P->M_aux);
-  int bt = 2;
-  while (bt < 4096 && 3.4 / bt > sqrt(32.0) * spacing) bt *= 2;
+  int bt = 2 * (int)lround(3.4 / (1.5 * spacing) / 2.0);
+  bt = bt < 2 ? 2 : (bt > 4096 ? 4096 : bt);
   build_tile_order(P->apx, P->apy, P->apz, P->M_aux, bt, 8192, P->tkeys, P->tvals, P->tkeys_alt, P->tvals_alt,
                    P->counts, &P->tile_order, s, &P->launches);
   return cuda_status(cudaGetLastError());

@@ -121,19 +121,22 @@ __device__ __forceinline__ float zeta_to_z(float zeta) {
 // enumeration in FP32. Every margin enlarges the enumerated set; the caller
 // decides membership with its own exact test.
 //
-// The longitude half-width of the cap at colatitude theta follows from the
-// spherical law of cosines; written as
-//   cos(dphi) = 1 - 2 sin((r + dt)/2) sin((r - dt)/2) / (sin(theta) sin(theta_q)),
+// The longitude half-width dphi of the cap at colatitude theta follows from
+// the spherical law of cosines; written as
+//   1 - cos(dphi) = 2 sin((r + dt)/2) sin((r - dt)/2) / (sin(theta) sin(theta_q)),
 // dt = theta - theta_q, it has no cancellation near the poles or near the
-// cap's rim. Band edges are colatitudes theta = 2 asin((1 - zeta)/sqrt 2)
-// (north) and pi - 2 asin((1 + zeta)/sqrt 2) (south), exact inverses of zeta(z).
+// cap's rim. Everything is carried as sines and cosines of half angles, so a
+// band costs products and square roots only: a band edge zeta has
+// sin(theta/2) = (1 - zeta)/sqrt 2 (zeta >= 0) or cos(theta/2) = (1 + zeta)/sqrt 2
+// (zeta < 0), the exact inverse of zeta(z); the half angles of (r + dt)/2 and
+// (r - dt)/2 follow by the addition theorems.
 struct Cap {
-  float th_q, s_q;          // colatitude of q and its sine
+  float zq, sq;             // cos and sin of the colatitude of q
+  float hs, hc;             // sin and cos of half the colatitude of q
+  float rs, rc;             // sin and cos of half the (widened) radius
   float cph, sph;           // cos/sin longitude of q
-  float r;                  // radius (widened)
   float zlo, zhi;           // z extent of the cap, widened (band index range)
-  float th_star, cstar;     // colatitude of the widest longitude extent, cos of that half-width
-  int north, south;         // the cap contains the north / south pole
+  float zstar, cstar;       // z of the widest longitude extent (3 if none), cos of that half-width
   int polar;                // enumerate whole bands (q at a pole, or a cap beyond ~86 degrees)
 };
 
@@ -142,8 +145,8 @@ __device__ __forceinline__ Cap make_cap_f(float fx, float fy, float fz, float rf
   const float PI_F = 3.14159265f;
   Cap c;
   const float sq = sqrtf(fx * fx + fy * fy);
-  c.th_q = atan2f(sq, fz);
-  c.s_q = sq;
+  c.zq = fz;
+  c.sq = sq;
   if (sq > 1e-12f) {
     c.cph = fx / sq;
     c.sph = fy / sq;
@@ -151,19 +154,28 @@ __device__ __forceinline__ Cap make_cap_f(float fx, float fy, float fz, float rf
     c.cph = 1.f;
     c.sph = 0.f;
   }
-  c.r = fminf(rf * (1.f + 2e-5f) + 2e-6f, PI_F);
-  c.north = c.th_q <= c.r;
-  c.south = (PI_F - c.th_q) <= c.r;
-  c.polar = (c.s_q < 1e-6f) || (c.r >= 1.5f);
-  c.zhi = c.north ? 1.f : fminf(1.f, cosf(c.th_q - c.r) + 4e-6f);
-  c.zlo = c.south ? -1.f : fmaxf(-1.f, cosf(c.th_q + c.r) - 4e-6f);
-  const float ratio = sinf(c.r) / fmaxf(c.s_q, 1e-30f);
+  const float r = fminf(rf * (1.f + 2e-5f) + 2e-6f, PI_F);
+  sincosf(0.5f * r, &c.rs, &c.rc);
+  if (fz >= 0.f) {
+    c.hc = sqrtf(0.5f * (1.f + fz));
+    c.hs = sq / (2.f * c.hc);
+  } else {
+    c.hs = sqrtf(0.5f * (1.f - fz));
+    c.hc = sq / (2.f * c.hs);
+  }
+  const float sr = 2.f * c.rs * c.rc, cr = (c.rc - c.rs) * (c.rc + c.rs);
+  const bool north = c.hs * c.rc <= c.hc * c.rs;   // theta_q <= r
+  const bool south = c.hc * c.rc <= c.hs * c.rs;   // theta_q + r >= pi
+  c.polar = (sq < 1e-6f) || (r >= 1.5f);
+  c.zhi = north ? 1.f : fminf(1.f, fz * cr + sq * sr + 4e-6f);
+  c.zlo = south ? -1.f : fmaxf(-1.f, fz * cr - sq * sr - 4e-6f);
+  const float ratio = sr / fmaxf(sq, 1e-30f);
   if (ratio < 1.f && !c.polar) {
     c.cstar = sqrtf(1.f - ratio * ratio);
-    c.th_star = acosf(fminf(1.f, fmaxf(-1.f, cosf(c.th_q) / cosf(c.r))));
+    c.zstar = fz / cr;                                // cos of the colatitude of the widest extent
   } else {
     c.cstar = -1.f;
-    c.th_star = -1.f;
+    c.zstar = 3.f;
   }
   return c;
 }
@@ -172,18 +184,28 @@ __device__ __forceinline__ Cap make_cap(double qx, double qy, double qz, double 
   return make_cap_f((float)qx, (float)qy, (float)qz, (float)r);
 }
 
-__device__ __forceinline__ float theta_of_zeta(float zeta) {
-  return zeta >= 0.f ? 2.f * asinf((1.f - zeta) * 0.70710678f)
-                     : 3.14159265f - 2.f * asinf((1.f + zeta) * 0.70710678f);
+// Half angles (a = sin(theta/2), b = cos(theta/2)) of the band edge zeta.
+__device__ __forceinline__ void edge_half_angles(float zeta, float& a, float& b) {
+  if (zeta >= 0.f) {
+    a = (1.f - zeta) * 0.70710678f;
+    b = sqrtf(fmaxf(0.f, 1.f - a * a));
+  } else {
+    b = (1.f + zeta) * 0.70710678f;
+    a = sqrtf(fmaxf(0.f, 1.f - b * b));
+  }
 }
 
-// cos of the cap's longitude half-width at colatitude th (inside the cap's
-// colatitude range); -1 when the geometry degenerates (whole band)
-__device__ __forceinline__ float cap_cos_halfwidth(const Cap& c, float th) {
-  const float den = sinf(th) * c.s_q;
+// cos of the cap's longitude half-width at the colatitude with half angles
+// (a, b): 1 where that colatitude is outside the cap's range (the band's part
+// of the cap then ends at the cap's rim, width 0), -1 where the whole circle
+// of latitude is inside or the geometry degenerates (whole band).
+__device__ __forceinline__ float cap_cos_halfwidth(const Cap& c, float a, float b) {
+  const float sdt = a * c.hc - b * c.hs, cdt = b * c.hc + a * c.hs;   // sin, cos of dt/2
+  const float sp = c.rs * cdt + c.rc * sdt, sm = c.rs * cdt - c.rc * sdt;
+  if (!(sp > 0.f) || !(sm > 0.f)) return 1.f;
+  const float den = 2.f * a * b * c.sq;
   if (!(den > 1e-12f)) return -1.f;
-  const float dt = th - c.th_q;
-  return 1.f - 2.f * sinf(0.5f * (c.r + dt)) * sinf(0.5f * (c.r - dt)) / den;
+  return 1.f - 2.f * sp * sm / den;
 }
 
 // The (at most two) contiguous runs of sorted points of band b that can lie
@@ -193,18 +215,17 @@ __device__ __forceinline__ void band_runs(const Cells& g, const Cap& c, int b, u
   n0 = n1 = 0;
   s0 = s1 = 0;
   const int B = g.B, P = g.P;
-  const float PI_F = 3.14159265f;
-  // band b spans zeta in [-1 + 2b/B, -1 + 2(b+1)/B): colatitudes [th_top, th_bot]
-  const float th_bot = theta_of_zeta(-1.f + 2.f * (float)b / (float)B);
-  const float th_top = theta_of_zeta(-1.f + 2.f * (float)(b + 1) / (float)B);
-  const float lo = fmaxf(th_top - 1e-6f, c.th_q - c.r);
-  const float hi = fminf(th_bot + 1e-6f, c.th_q + c.r);
-  if (lo > hi) return;                                      // band outside the cap's colatitudes
+  // band b spans zeta in [-1 + 2b/B, -1 + 2(b+1)/B)
+  float ab, bb, at, bt;
+  edge_half_angles(-1.f + 2.f * (float)b / (float)B, ab, bb);
+  edge_half_angles(-1.f + 2.f * (float)(b + 1) / (float)B, at, bt);
+  const float z_bot = (bb - ab) * (bb + ab), z_top = (bt - at) * (bt + at);
+  if (z_top < c.zlo || z_bot > c.zhi) return;               // band outside the cap's colatitudes
   const uint32_t base = (uint32_t)b * (uint32_t)P;
-  bool full = c.polar || (c.north && lo <= c.r - c.th_q) || (c.south && hi >= 2.f * PI_F - c.r - c.th_q);
+  bool full = c.polar;
   if (!full) {
-    float cmin = fminf(cap_cos_halfwidth(c, fmaxf(lo, 0.f)), cap_cos_halfwidth(c, fminf(hi, PI_F)));
-    if (c.th_star >= 0.f && c.th_star > lo - 1e-4f && c.th_star < hi + 1e-4f) cmin = fminf(cmin, c.cstar);
+    float cmin = fminf(cap_cos_halfwidth(c, at, bt), cap_cos_halfwidth(c, ab, bb));
+    if (c.zstar > z_bot - 1e-4f && c.zstar < z_top + 1e-4f) cmin = fminf(cmin, c.cstar);
     cmin = cmin - 2e-5f * (1.f - cmin) - 1e-6f;
     full = !(cmin > 0.f);
     if (!full) {
@@ -258,7 +279,7 @@ __device__ __forceinline__ void for_cap_candidates(const Cells& g, const Cap& c,
   const int lane = threadIdx.x & 31;
   int b_lo, b_hi;
   cap_band_range(g, c, b_lo, b_hi);
-  const int bc = MIDOUT ? min(max(band_of_f(cosf(c.th_q), g.B), b_lo), b_hi) : b_lo;
+  const int bc = MIDOUT ? min(max(band_of_f(c.zq, g.B), b_lo), b_hi) : b_lo;
   const int span = MIDOUT ? 2 * max(bc - b_lo, b_hi - bc) + 1 : b_hi - b_lo + 1;
   for (int k0 = 0; k0 < span; k0 += 32) {
     const int k = k0 + lane;

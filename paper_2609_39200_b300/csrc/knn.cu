@@ -26,7 +26,7 @@ __device__ __forceinline__ double c2_margin(double c2) { return 1e-6 * sqrt(c2) 
 // n-th smallest exact squared chord from q to the points of g (+inf when the
 // set has fewer than n points), keeping exact FP64 chords throughout. `list`
 // is this warp's shared scratch (n doubles). Slow path of knn_nth.
-__device__ double knn_nth_exact(const Cells& g, double qx, double qy, double qz, int n, double* list, double r0,
+__device__ __noinline__ double knn_nth_exact(const Cells& g, double qx, double qy, double qz, int n, double* list, double r0,
                                 bool* failed) {
   const int lane = threadIdx.x & 31;
   const float qxf = (float)qx, qyf = (float)qy, qzf = (float)qz;
@@ -140,7 +140,7 @@ constexpr int KNN_SCRATCH = KNN_MAX * 8 + 32 * 4;      // warp scratch: exact-pa
 
 // Phase 1 of a search without a known radius: a radius whose candidate
 // enumeration (counted from the run table alone) holds a few times n points.
-__device__ float knn_initial_radius(const Cells& g, float qxf, float qyf, float qzf, int n, float r0) {
+__device__ __noinline__ float knn_initial_radius(const Cells& g, float qxf, float qyf, float qzf, int n, float r0) {
   const float PI_F = 3.14159265f;
   float r = fminf(fmaxf(r0, 1e-7f), PI_F), rlo = 0.f, rhi = PI_F;
   bool have_lo = false, have_hi = false;
@@ -176,10 +176,39 @@ __device__ float knn_initial_radius(const Cells& g, float qxf, float qyf, float 
 
 __device__ __forceinline__ float geodesic_f(float c2) { return 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2))); }
 
+// A radius beyond r for a cap that held fewer than n points: the enumeration
+// at the new radius (counted from the run table alone) holds about 2 to 8
+// times as many points as at r, so the scans of a search grow geometrically
+// in work even where the radius must cross an empty region (a hole in the
+// node set) and a fixed radius factor would add a huge annulus.
+__device__ __noinline__ float knn_grow_radius(const Cells& g, float qxf, float qyf, float qzf, float r, int n) {
+  const float PI_F = 3.14159265f;
+  const uint32_t bc0 = cap_box_count(g, make_cap_f(qxf, qyf, qzf, r));
+  const uint32_t lowT = max(2u * bc0, (uint32_t)n + (uint32_t)n / 4 + 4u), highT = 4u * lowT + 64u;
+  float rlo = r, rhi = PI_F, d = 0.125f;
+  bool have_hi = false;
+  for (int it = 0; it < 60; ++it) {
+    const float r1 = have_hi ? sqrtf(rlo * rhi) : fminf(rlo * (1.f + d) + 1e-6f, PI_F);
+    const uint32_t bc = cap_box_count(g, make_cap_f(qxf, qyf, qzf, r1));
+    if (bc < lowT) {
+      if (r1 >= PI_F) return PI_F;
+      rlo = r1;
+      d *= 2.f;
+    } else if (bc > highT) {
+      rhi = r1;
+      have_hi = true;
+    } else {
+      return r1;
+    }
+    if (have_hi && rhi < rlo * 1.002f) return rhi;
+  }
+  return have_hi ? rhi : PI_F;
+}
+
 // One scan of the cap of radius r. Every lane keeps, in registers, the KL
 // smallest FP32 squared chords among the candidates it is dealt (sorted,
 // with indices) - no warp-serialised list. The n-th smallest key T over the
-// warp is bracketed, tl < T <= th, by a bisection on values that stops once
+// warp is bracketed, tl < T <= th, by a search on values that stops once
 // th - tl is within the FP32 error bound m or (tl, th] holds one key. Then
 // keys < tl - 2m are certainly among the n nearest (A of them), keys above
 // th + 2m certainly not, and the answer is the (n - A)-th smallest exact FP64
@@ -225,41 +254,41 @@ __device__ int knn_select(const Cells& g, double qx, double qy, double qz, float
   int fin = 0;
 #pragma unroll
   for (int s2 = 0; s2 < KL; ++s2) fin += key[s2] < INF_F ? 1 : 0;
-  if (warp_sum(fin) < n) {                          // fewer than n points in the cap
+  const int fin_total = warp_sum(fin);
+  if (fin_total < n) {                          // fewer than n points in the cap
     if (__any_sync(FULL, key[KL - 1] < INF_F)) return 2;  // unless a lane list overflowed
-    r_next = fminf(PI_F, 2.f * r);
+    r_next = knn_grow_radius(g, qxf, qyf, qzf, r, n);
     return 1;
   }
-  // Isolate the n-th smallest key T in a window [tl, th] with count(<= tl) < n
-  // <= count(<= th) by bisection on values, stopping once the window is
-  // narrower than the FP32 error bound (or holds the n-th key alone); the
-  // uncertain set below is then taken around that window.
-  float tl = __uint_as_float(0x7f7fffffu), th = 0.f;
+  // Isolate the n-th smallest key T in a window (tl, th] with cl = count(<= tl)
+  // < n <= ch = count(<= th): interpolation on the counts (the keys are
+  // roughly uniform in squared chord, i.e. in area), safeguarded to cut at
+  // least an eighth of the window, until the window holds one key or is
+  // narrower than the FP32 error bound.
+  float th = 0.f;
 #pragma unroll
   for (int s2 = 0; s2 < KL; ++s2)
     if (key[s2] < INF_F) th = fmaxf(th, key[s2]);
-  tl = fminf(tl, key[0]);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    tl = fminf(tl, __shfl_xor_sync(FULL, tl, o));
-    th = fmaxf(th, __shfl_xor_sync(FULL, th, o));
-  }
-  tl = tl * (1.f - 1e-6f) - 1e-30f;                 // count(<= tl) = 0 < n; count(<= th) >= n
-  for (int it = 0; it < 40; ++it) {
-    if (th - tl <= c2_margin_f(th)) break;
-    const float mid = 0.5f * (tl + th);
+  for (int o = 16; o > 0; o >>= 1) th = fmaxf(th, __shfl_xor_sync(FULL, th, o));
+  float tl = -1e-30f;
+  int cl = 0, ch = fin_total;
+  for (int it = 0; it < 48 && ch - cl > 1; ++it) {
+    const float w = th - tl;
+    if (w <= c2_margin_f(th)) break;
+    float f = __fdividef((float)(n - cl) - 0.5f, (float)(ch - cl));
+    f = fminf(fmaxf(f, 0.125f), 0.875f);
+    const float mid = tl + w * f;
     int cnt = 0;
 #pragma unroll
     for (int s2 = 0; s2 < KL; ++s2) cnt += key[s2] <= mid ? 1 : 0;
     const int c = warp_sum(cnt);
-    if (c >= n) th = mid;
-    else tl = mid;
-    // stop when (tl, th] holds exactly one key value (the n-th)
-    if (c == n || c == n - 1) {
-      int inwin = 0;
-#pragma unroll
-      for (int s2 = 0; s2 < KL; ++s2) inwin += (key[s2] > tl && key[s2] <= th) ? 1 : 0;
-      if (warp_sum(inwin) <= 1) break;
+    if (c >= n) {
+      th = mid;
+      ch = c;
+    } else {
+      tl = mid;
+      cl = c;
     }
   }
   const float m = c2_margin_f(th);
@@ -302,7 +331,8 @@ __device__ int knn_select(const Cells& g, double qx, double qy, double qz, float
   // every point within geodesic r of q was enumerated; is the n-th inside?
   const float gn = geodesic_f((float)nth);
   if (gn * (1.f + 2e-6f) <= r || r >= PI_F) return 0;
-  r_next = fminf(PI_F, fmaxf(1.25f * r, gn * (1.f + 1e-5f) + 1e-6f));
+  // the cap through the n-th candidate holds n points: the next scan is final
+  r_next = fminf(PI_F, gn * (1.f + 1e-5f) + 1e-6f);
   return 1;
 }
 
@@ -332,12 +362,13 @@ __device__ double knn_nth(const Cells& g, double qx, double qy, double qz, int n
   return __longlong_as_double(0x7ff0000000000000ll);
 }
 
-// d_n at the auxiliary points. A warp walks chunks of 32 consecutive points of
-// a spatially coherent order (coarse latitude bands, then longitude; chunks
-// handed out dynamically). Each search starts from the previous point's exact
-// d_n plus the distance between the two points: d_n is 1-Lipschitz, so that
-// cap holds at least n nodes and one scan suffices. The 32 exact chords of a
-// chunk become geodesic distances together (one FP64 asin per lane).
+// d_n at the auxiliary points. A warp walks chunks of AK_CHUNK consecutive
+// points of a spatially coherent order (thin latitude bands, then longitude;
+// chunks handed out dynamically). Each search starts from the previous
+// point's exact d_n plus the distance between the two points: d_n is
+// 1-Lipschitz, so that cap holds at least n nodes and one scan suffices. The
+// exact chords of a chunk become geodesic distances together, 32 per FP64
+// asin instruction.
 constexpr int AK_WARPS = 4;
 constexpr int AK_CHUNK = 32;
 
@@ -348,6 +379,7 @@ __global__ void __launch_bounds__(AK_WARPS * 32) aux_knn_kernel(Cells nodes, Cel
                                                                 float* __restrict__ dn_f, DevStatus* st,
                                                                 unsigned long long* ctr) {
   __shared__ __align__(16) unsigned char scr[AK_WARPS][KNN_SCRATCH];
+  __shared__ double res[AK_WARPS][AK_CHUNK];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
     unsigned long long t = 0;
@@ -357,7 +389,6 @@ __global__ void __launch_bounds__(AK_WARPS * 32) aux_knn_kernel(Cells nodes, Cel
     if (first >= aux.n) break;
     const int cnt = (int)min((long long)AK_CHUNK, (long long)aux.n - first);
     float prev = -1.f, pxf = 0.f, pyf = 0.f, pzf = 0.f;
-    double mine = 0.0;
     bool failed = false;
     for (int k = 0; k < cnt; ++k) {
       const uint32_t fi = order[first + k];
@@ -373,15 +404,19 @@ __global__ void __launch_bounds__(AK_WARPS * 32) aux_knn_kernel(Cells nodes, Cel
       pxf = axf;
       pyf = ayf;
       pzf = azf;
-      if (lane == k) mine = c2;
+      if (lane == 0) res[warp][k] = c2;
     }
-    if (lane < cnt) {
-      if (failed || !(mine < 1e300)) set_flag(st, ST_KNN);
-      const uint32_t fi = order[first + lane];
-      const double dn = geodesic_from_chord2(mine);
+    __syncwarp();
+    if (failed && lane == 0) set_flag(st, ST_KNN);
+    for (int k = lane; k < cnt; k += 32) {
+      const double c2 = res[warp][k];
+      if (!(c2 < 1e300)) set_flag(st, ST_KNN);
+      const uint32_t fi = order[first + k];
+      const double dn = geodesic_from_chord2(c2);
       dn_sorted[fi] = dn;
       dn_f[fi] = (float)dn;
     }
+    __syncwarp();
   }
 }
 
