@@ -88,10 +88,10 @@ typedef struct {
   int64_t grid_nodes;     /* M_Q */
   int64_t aux_points;     /* size of the auxiliary grid */
   int32_t bands, cells;   /* neighbour structure: latitude bands and cells per band */
-  int64_t knn_candidates; /* auxiliary k-NN: candidates streamed by the tile search */
-  int64_t knn_insertions; /* auxiliary k-NN: per-point heap insertions */
-  int64_t knn_lane_fallbacks;   /* auxiliary points resolved by a single-point search */
-  int64_t knn_exact_fallbacks;  /* single-point searches that needed all-FP64 distances */
+  int64_t knn_candidates; /* auxiliary k-NN: candidate nodes streamed, over all cap scans */
+  int64_t knn_scans;      /* auxiliary k-NN: cap scans (one per point when the chained radius
+                             already holds n nodes) */
+  int64_t knn_exact_fallbacks;  /* auxiliary searches that needed all-FP64 distances */
 } hamls_fit_stats;
 
 /* Fill *p with the defaults listed in hamls_params. */

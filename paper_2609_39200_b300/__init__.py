@@ -47,7 +47,7 @@ class FitStats(ctypes.Structure):
                 ("n_regularized", ctypes.c_int64), ("n_guarded", ctypes.c_int64), ("n_fp64_redo", ctypes.c_int64),
                 ("n_dropped", ctypes.c_int64), ("grid_nodes", ctypes.c_int64), ("aux_points", ctypes.c_int64),
                 ("bands", ctypes.c_int32), ("cells", ctypes.c_int32), ("knn_candidates", ctypes.c_int64),
-                ("knn_insertions", ctypes.c_int64), ("knn_lane_fallbacks", ctypes.c_int64),
+                ("knn_scans", ctypes.c_int64),
                 ("knn_exact_fallbacks", ctypes.c_int64)]
 
     def as_dict(self):

@@ -614,8 +614,7 @@ hamls_status hamls_stats(hamls_plan_t P, hamls_fit_stats* out) {
   out->bands = P->B;
   out->cells = P->P;
   out->knn_candidates = (int64_t)d.cnt[C_KNN_CAND];
-  out->knn_insertions = (int64_t)d.cnt[C_KNN_INS];
-  out->knn_lane_fallbacks = (int64_t)d.cnt[C_KNN_LANE_FB];
+  out->knn_scans = (int64_t)d.cnt[C_KNN_SCAN];
   out->knn_exact_fallbacks = (int64_t)d.cnt[C_KNN_EXACT_FB];
   return HAMLS_OK;
 }

@@ -216,9 +216,14 @@ __device__ __noinline__ float knn_grow_radius(const Cells& g, float qxf, float q
 // Returns 0 with the exact n-th chord in nth, 1 when the cap was too small
 // (r_next to retry), 2 when a lane's list may have dropped a needed key or
 // too many keys are uncertain (the caller runs the exact search).
+// Per-lane tallies of a search (summed over the warp when reported).
+struct KnnTally {
+  uint32_t cand = 0, scans = 0;
+};
+
 template <int KL>
 __device__ int knn_select(const Cells& g, double qx, double qy, double qz, float r, int n, uint32_t* ustage,
-                          double& nth, float& r_next) {
+                          double& nth, float& r_next, KnnTally& tally) {
   const int lane = threadIdx.x & 31;
   const float PI_F = 3.14159265f;
   const float INF_F = __int_as_float(0x7f800000);
@@ -231,24 +236,25 @@ __device__ int knn_select(const Cells& g, double qx, double qy, double qz, float
     kid[s2] = 0xFFFFFFFFu;
   }
   Cap c = make_cap_f(qxf, qyf, qzf, r);
+  ++tally.scans;
   for_cap_candidates<true>(g, c, [&](bool valid, uint32_t idx) {
     if (!valid) return;
+    ++tally.cand;
     const float4 p = g.pf[idx];
     const float dx = p.x - qxf, dy = p.y - qyf, dz = p.z - qzf;
-    float x = dx * dx + dy * dy + dz * dz;
+    const float x = dx * dx + dy * dy + dz * dz;
     if (x < key[KL - 1]) {
-      uint32_t xi = idx;
+      // insert after equal keys: every slot decides from the old list at once
+      bool gt[KL];
 #pragma unroll
-      for (int s2 = 0; s2 < KL; ++s2) {
-        if (x < key[s2]) {
-          const float t = key[s2];
-          key[s2] = x;
-          x = t;
-          const uint32_t ti = kid[s2];
-          kid[s2] = xi;
-          xi = ti;
-        }
+      for (int s2 = 0; s2 < KL; ++s2) gt[s2] = key[s2] > x;
+#pragma unroll
+      for (int s2 = KL - 1; s2 > 0; --s2) {
+        key[s2] = gt[s2] ? (gt[s2 - 1] ? key[s2 - 1] : x) : key[s2];
+        kid[s2] = gt[s2] ? (gt[s2 - 1] ? kid[s2 - 1] : idx) : kid[s2];
       }
+      key[0] = gt[0] ? x : key[0];
+      kid[0] = gt[0] ? idx : kid[0];
     }
   });
   int fin = 0;
@@ -342,14 +348,15 @@ __device__ int knn_select(const Cells& g, double qx, double qy, double qz, float
 // KL: length of the per-lane lists, 12 for n <= 48, else 16.
 template <int KL>
 __device__ double knn_nth(const Cells& g, double qx, double qy, double qz, int n, unsigned char* scratch,
-                          double r0, bool* failed, unsigned long long* exact_fb = nullptr, float r_hint = -1.f) {
+                          double r0, bool* failed, KnnTally& tally,
+                          unsigned long long* exact_fb = nullptr, float r_hint = -1.f) {
   const float qxf = (float)qx, qyf = (float)qy, qzf = (float)qz;
   float r = r_hint > 0.f ? fminf(r_hint, 3.14159265f) : knn_initial_radius(g, qxf, qyf, qzf, n, (float)r0);
   uint32_t* ustage = reinterpret_cast<uint32_t*>(scratch + KNN_MAX * 8);
   for (int it = 0; it < 64; ++it) {
     double nth;
     float rn = r;
-    const int rc = knn_select<KL>(g, qx, qy, qz, r, n, ustage, nth, rn);
+    const int rc = knn_select<KL>(g, qx, qy, qz, r, n, ustage, nth, rn, tally);
     if (rc == 0) return nth;
     if (rc == 2) {
       if (exact_fb && (threadIdx.x & 31) == 0) atomicAdd(exact_fb, 1ull);
@@ -381,6 +388,7 @@ __global__ void __launch_bounds__(AK_WARPS * 32) aux_knn_kernel(Cells nodes, Cel
   __shared__ __align__(16) unsigned char scr[AK_WARPS][KNN_SCRATCH];
   __shared__ double res[AK_WARPS][AK_CHUNK];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  KnnTally tally;
   for (;;) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(ctr, 1ull);
@@ -399,7 +407,8 @@ __global__ void __launch_bounds__(AK_WARPS * 32) aux_knn_kernel(Cells nodes, Cel
         const float dx = axf - pxf, dy = ayf - pyf, dz = azf - pzf;
         hint = (prev + geodesic_f(dx * dx + dy * dy + dz * dz)) * (1.f + 1e-5f) + 2e-6f;
       }
-      const double c2 = knn_nth<KL>(nodes, ax, ay, az, n, scr[warp], r0, &failed, &st->cnt[C_KNN_EXACT_FB], hint);
+      const double c2 = knn_nth<KL>(nodes, ax, ay, az, n, scr[warp], r0, &failed, tally, &st->cnt[C_KNN_EXACT_FB],
+                                    hint);
       prev = (c2 < 1e300) ? geodesic_f((float)c2) : -1.f;
       pxf = axf;
       pyf = ayf;
@@ -418,6 +427,11 @@ __global__ void __launch_bounds__(AK_WARPS * 32) aux_knn_kernel(Cells nodes, Cel
     }
     __syncwarp();
   }
+  const unsigned long long cand = warp_sum((unsigned long long)tally.cand);
+  if (lane == 0) {
+    atomicAdd(&st->cnt[C_KNN_CAND], cand);
+    atomicAdd(&st->cnt[C_KNN_SCAN], (unsigned long long)tally.scans);
+  }
 }
 
 template <int KL>
@@ -429,7 +443,8 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_query_kernel(Cells nodes, 
   const int64_t nw = (int64_t)gridDim.x * KNN_WARPS;
   for (int64_t i = (int64_t)blockIdx.x * KNN_WARPS + warp; i < nq; i += nw) {
     bool failed = false;
-    double c2 = knn_nth<KL>(nodes, q[3 * i], q[3 * i + 1], q[3 * i + 2], n, lists[warp], r0, &failed);
+    KnnTally tally;
+    double c2 = knn_nth<KL>(nodes, q[3 * i], q[3 * i + 1], q[3 * i + 2], n, lists[warp], r0, &failed, tally);
     if (lane == 0) {
       if (failed) set_flag(st, ST_KNN);
       out[i] = c2;
@@ -578,7 +593,8 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) guard_kernel(SupportArgs a, do
     const int k = j / L, jj = j - k * L;
     const double qx = a.ring_s[k] * a.cphi[jj], qy = a.ring_s[k] * a.sphi[jj], qz = a.ring_t[k];
     bool failed = false;
-    double c2 = knn_nth<KL_MAX>(a.nodes, qx, qy, qz, a.n_target, lists[warp], r0, &failed);
+    KnnTally tally;
+    double c2 = knn_nth<KL_MAX>(a.nodes, qx, qy, qz, a.n_target, lists[warp], r0, &failed, tally);
     double delta = (1.0 + a.eps) * geodesic_from_chord2(c2);
     const double PI = 3.14159265358979323846;
     bool bad = failed || !(delta < 0.5 * PI);
