@@ -106,7 +106,8 @@ __device__ __forceinline__ int cell_of_f(float x, float y, int P) {
   else if (x < 0.f && y <= 0.f) { q = 2; num = ay; }
   else if (x >= 0.f && y < 0.f) { q = 3; num = ax; }
   else { q = 0; num = 0.f; }
-  float frac = den > 0.f ? num / den : 0.f;
+  // approximate division: the runs built from this cell carry a one-cell margin
+  float frac = den > 0.f ? __fdividef(num, den) : 0.f;
   int qc = P / 4;
   int w = min(max((int)floorf(frac * (float)qc), 0), qc - 1);
   return q * qc + w;
@@ -147,9 +148,12 @@ __device__ __forceinline__ Cap make_cap_f(float fx, float fy, float fz, float rf
   const float sq = sqrtf(fx * fx + fy * fy);
   c.zq = fz;
   c.sq = sq;
+  // approximate divisions below: their 2-ulp errors are far inside the
+  // margins added to the half-widths and to the runs
   if (sq > 1e-12f) {
-    c.cph = fx / sq;
-    c.sph = fy / sq;
+    const float isq = __fdividef(1.f, sq);
+    c.cph = fx * isq;
+    c.sph = fy * isq;
   } else {
     c.cph = 1.f;
     c.sph = 0.f;
@@ -158,10 +162,10 @@ __device__ __forceinline__ Cap make_cap_f(float fx, float fy, float fz, float rf
   sincosf(0.5f * r, &c.rs, &c.rc);
   if (fz >= 0.f) {
     c.hc = sqrtf(0.5f * (1.f + fz));
-    c.hs = sq / (2.f * c.hc);
+    c.hs = __fdividef(sq, 2.f * c.hc);
   } else {
     c.hs = sqrtf(0.5f * (1.f - fz));
-    c.hc = sq / (2.f * c.hs);
+    c.hc = __fdividef(sq, 2.f * c.hs);
   }
   const float sr = 2.f * c.rs * c.rc, cr = (c.rc - c.rs) * (c.rc + c.rs);
   const bool north = c.hs * c.rc <= c.hc * c.rs;   // theta_q <= r
@@ -169,10 +173,10 @@ __device__ __forceinline__ Cap make_cap_f(float fx, float fy, float fz, float rf
   c.polar = (sq < 1e-6f) || (r >= 1.5f);
   c.zhi = north ? 1.f : fminf(1.f, fz * cr + sq * sr + 4e-6f);
   c.zlo = south ? -1.f : fmaxf(-1.f, fz * cr - sq * sr - 4e-6f);
-  const float ratio = sr / fmaxf(sq, 1e-30f);
+  const float ratio = __fdividef(sr, fmaxf(sq, 1e-30f));
   if (ratio < 1.f && !c.polar) {
     c.cstar = sqrtf(1.f - ratio * ratio);
-    c.zstar = fz / cr;                                // cos of the colatitude of the widest extent
+    c.zstar = __fdividef(fz, cr);                     // cos of the colatitude of the widest extent
   } else {
     c.cstar = -1.f;
     c.zstar = 3.f;
@@ -205,7 +209,7 @@ __device__ __forceinline__ float cap_cos_halfwidth(const Cap& c, float a, float 
   if (!(sp > 0.f) || !(sm > 0.f)) return 1.f;
   const float den = 2.f * a * b * c.sq;
   if (!(den > 1e-12f)) return -1.f;
-  return 1.f - 2.f * sp * sm / den;
+  return 1.f - __fdividef(2.f * sp * sm, den);
 }
 
 // The (at most two) contiguous runs of sorted points of band b that can lie
@@ -215,10 +219,11 @@ __device__ __forceinline__ void band_runs(const Cells& g, const Cap& c, int b, u
   n0 = n1 = 0;
   s0 = s1 = 0;
   const int B = g.B, P = g.P;
-  // band b spans zeta in [-1 + 2b/B, -1 + 2(b+1)/B)
+  // band b spans zeta in [-1 + 2b/B, -1 + 2(b+1)/B); 2/B exactly (B a power of two)
+  const float zstep = (B & (B - 1)) == 0 ? __int_as_float((128 - (__ffs(B) - 1)) << 23) : 2.f / (float)B;
   float ab, bb, at, bt;
-  edge_half_angles(-1.f + 2.f * (float)b / (float)B, ab, bb);
-  edge_half_angles(-1.f + 2.f * (float)(b + 1) / (float)B, at, bt);
+  edge_half_angles(-1.f + (float)b * zstep, ab, bb);
+  edge_half_angles(-1.f + (float)(b + 1) * zstep, at, bt);
   const float z_bot = (bb - ab) * (bb + ab), z_top = (bt - at) * (bt + at);
   if (z_top < c.zlo || z_bot > c.zhi) return;               // band outside the cap's colatitudes
   const uint32_t base = (uint32_t)b * (uint32_t)P;
