@@ -82,7 +82,8 @@ typedef struct {
   int64_t sum_n;          /* sum over grid nodes of n(q) = #X(q) (eq. number_of_local_nodes) */
   int64_t min_n, max_n;
   int64_t n_regularized;  /* grid nodes with tau~ > 0 */
-  int64_t n_guarded;      /* grid nodes whose support came from the exact-d_n guard */
+  int64_t n_guarded;      /* grid nodes whose support came from the exact-d_n guard; the guard
+                             runs inside the first fit after a plan/replan */
   int64_t n_fp64_redo;    /* MIXED: grid nodes whose local solve ran in FP64 */
   int64_t n_dropped;      /* basis directions dropped by the pivot floor, summed */
   int64_t grid_nodes;     /* M_Q */
@@ -100,8 +101,9 @@ void hamls_default_params(hamls_params* p);
 /*
  * hamls_plan - allocate a plan for up to M nodes at bandwidth N and degree K
  * and build everything that depends on the nodes only: the quadrature grid
- * (Sec. 2.1), the cell list over the nodes, d_n on the auxiliary grid,
- * delta(q) and n(q) at every grid node (Sec. 2.2).
+ * (Sec. 2.1), the cell list over the nodes, d_n on the auxiliary grid and
+ * delta(q) at every grid node (Sec. 2.2). n(q) = #X(q) is counted by the
+ * fit's gather, which also applies the guard (exact d_n at q) where n(q) < m.
  *   out          receives the plan handle (NULL on failure)
  *   nodes_xyz    M x 3 doubles, row-major unit vectors x_i (host or device)
  *   node_weights M doubles v_i > 0 multiplying the MLS weights, e.g. Voronoi
@@ -140,7 +142,8 @@ hamls_status hamls_fit(hamls_plan_t plan, const double* values, double* coeffs, 
  * return the first device-detected error, or HAMLS_OK. Clears the status. */
 hamls_status hamls_sync(hamls_plan_t plan, int timeout_ms);
 
-/* Statistics of the last plan/replan and fit (synchronises the stream). */
+/* Statistics of the last plan/replan and fit (synchronises the stream); the
+ * n(q) figures (sum_n, min_n, max_n, n_guarded) come from the last fit. */
 hamls_status hamls_stats(hamls_plan_t plan, hamls_fit_stats* out);
 
 /* Release every resource of the plan (synchronises its last stream). */
@@ -154,8 +157,8 @@ const char* hamls_status_string(hamls_status s);
  * around each stage on the caller's stream; hamls_stage_times returns the
  * elapsed milliseconds of the last call of each stage (synchronises):
  *   0 cell keys + sort + ranges, 1 auxiliary kNN, 2 Shepard + support radius,
- *   3 neighbour counts + guard + ordering, 4 value staging, 5 MLS,
- *   6 ring FFT, 7 Legendre quadrature.  n_out receives the count (8).
+ *   3 work order of the grid nodes, 4 value staging, 5 MLS (gather with n(q),
+ *   guard, solve), 6 ring FFT, 7 Legendre quadrature.  n_out receives the count (8).
  */
 hamls_status hamls_set_timing(hamls_plan_t plan, int enable);
 hamls_status hamls_stage_times(hamls_plan_t plan, float* ms, int capacity, int* n_out);

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_HERE, "libhamls.so")
 HAMLS_FP64, HAMLS_MIXED = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "cuda error", 4: "underdetermined",
           5: "support too large", 6: "timeout", 7: "non-finite value", 8: "capacity exceeded"}
-STAGES = ("cells", "aux_knn", "shepard", "counts", "stage_values", "mls", "fft", "legendre")
+STAGES = ("cells", "aux_knn", "shepard", "order", "stage_values", "mls", "fft", "legendre")
 
 
 class HamlsError(RuntimeError):

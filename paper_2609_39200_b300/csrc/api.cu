@@ -61,7 +61,10 @@ __global__ void reset_status_kernel(DevStatus* st, int full) {
       for (int i = 0; i < 16; ++i) st->cnt[i] = 0;
       st->cnt[C_MIN_N] = ~0ull;
     } else {
+      // per fit: the gather recounts n(q) and re-runs the guard
       st->cnt[C_REG] = st->cnt[C_REDO] = st->cnt[C_DROP] = st->cnt[C_BATCH] = st->cnt[C_REDO_LIST] = 0;
+      st->cnt[C_SUM_N] = st->cnt[C_MAX_N] = st->cnt[C_GUARD] = st->cnt[C_GUARD_LIST] = st->cnt[C_LIST_BATCH] = 0;
+      st->cnt[C_MIN_N] = ~0ull;
     }
   }
 }
@@ -278,6 +281,7 @@ SupportArgs support_args(hamls_plan_s* P) {
   a.guard_list = P->guard_list;
   a.order_keys = P->okeys;
   a.order_vals = P->ovals;
+  a.order = P->order;
   a.fp64 = P->mixed ? 0 : 1;
   a.tile_order = P->tile_order;
   a.num_sms = P->num_sms;
@@ -334,7 +338,6 @@ hamls_status build_nodes(hamls_plan_s* P, const double* nodes, const double* wts
   run_shepard(a, s, &P->launches);
   stage_end(P, 2, s);
   stage_begin(P, 3, s);
-  run_counts(a, s, &P->launches);
   bool alt = radix_sort_pairs(P->okeys, P->ovals, P->okeys_alt, P->ovals_alt, P->MQ, 20, P->counts, s,
                               &P->launches);
   P->order = alt ? P->ovals_alt : P->ovals;
@@ -545,10 +548,16 @@ hamls_status hamls_fit(hamls_plan_t P, const double* values, double* coeffs, cud
   for (int l = 0; l <= KMAX; ++l) a.mu[l] = pow((double)l * (l + 1), P->p.sobolev_s);
   a.mom = P->mom;
   a.redo_list = P->redo_list;
+  a.m = P->m;
+  a.count = P->count;
+  a.guarded = P->guarded;
+  a.guard_list = P->guard_list;
   a.st = P->st;
   a.num_sms = P->num_sms;
   stage_begin(P, 5, s);
-  run_mls(a, P->mixed, s, &P->launches);
+  run_mls(a, P->mixed, s, &P->launches, 1);
+  run_guard(support_args(P), s, &P->launches);
+  run_mls(a, P->mixed, s, &P->launches, 2);
   stage_end(P, 5, s);
   const bool dev_out = is_device_ptr(coeffs);
   QuadArgs q;

@@ -34,7 +34,7 @@ enum : unsigned {
 
 // device counters
 enum { C_SUM_N = 0, C_MIN_N, C_MAX_N, C_REG, C_GUARD, C_REDO, C_DROP, C_GUARD_LIST, C_REDO_LIST,
-       C_BATCH, C_TILE, C_KNN_CAND, C_KNN_SCAN, C_KNN_EXACT_FB, C_NCOUNT };
+       C_BATCH, C_TILE, C_KNN_CAND, C_KNN_SCAN, C_KNN_EXACT_FB, C_LIST_BATCH, C_NCOUNT };
 
 struct DevStatus {
   unsigned flags;

@@ -67,7 +67,8 @@ struct SupportArgs {
   const float *tf, *sf, *cpf, *spf;
   int32_t* count;               // M_Q
   uint8_t* guarded;             // M_Q
-  uint32_t* guard_list;         // M_Q
+  uint32_t* guard_list;         // work-order positions whose support holds fewer than m nodes
+  const uint32_t* order;        // work order (position -> grid node)
   uint32_t* order_keys;         // M_Q (cost keys)
   uint32_t* order_vals;         // M_Q
   int fp64;                     // 1: FP64 Shepard, 0: FP32
@@ -77,7 +78,8 @@ struct SupportArgs {
 };
 void run_aux_knn(const SupportArgs& a, cudaStream_t s, int64_t* launches);
 void run_shepard(const SupportArgs& a, cudaStream_t s, int64_t* launches);
-void run_counts(const SupportArgs& a, cudaStream_t s, int64_t* launches);
+// the guard of the listed work-order positions (Sec. 2.2): exact d_n at q
+void run_guard(const SupportArgs& a, cudaStream_t s, int64_t* launches);
 void run_knn_queries(const Cells& nodes, const double* q, int64_t nq, int n, double* c2_out, DevStatus* st,
                      cudaStream_t s, int64_t* launches);
 void run_ball_queries(const Cells& nodes, const double* q, const double* rho2, int64_t nq, int64_t* count,
@@ -105,10 +107,16 @@ struct MlsArgs {
   double mu[KMAX + 1];
   void* mom;                    // per work-order position: moments (float MIXED, double FP64)
   uint32_t* redo_list;          // MIXED: work-order positions re-solved in FP64
+  int m;                        // dim Pi_K^tan
+  int32_t* count;               // M_Q: n(q) = #X(q), written by the gather
+  const uint8_t* guarded;       // M_Q: support radius from the guard
+  uint32_t* guard_list;         // work-order positions with n(q) < m
   DevStatus* st;
   int num_sms;
 };
-void run_mls(const MlsArgs& a, bool mixed, cudaStream_t s, int64_t* launches);
+// part 1: gather every grid node (moments, n(q), guard list);
+// part 2: gather the guard list again, then solve (and re-solve in FP64)
+void run_mls(const MlsArgs& a, bool mixed, cudaStream_t s, int64_t* launches, int part);
 int mls_moment_slots(int K);
 
 // ------------------------------------------------------------------- quad.cu

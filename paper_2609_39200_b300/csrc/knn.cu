@@ -453,6 +453,13 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_query_kernel(Cells nodes, 
 }
 
 // --------------------------------------------------------- Shepard / delta
+// Work-order key of a grid node, heaviest first: the support radius stands in
+// for the node's cost (large radii sit in holes of the node set, where a cap
+// collects its nodes from a long rim).
+__device__ __forceinline__ uint32_t order_key(float delta) {
+  return 0xFFFFFu - (uint32_t)(fminf(fmaxf(delta, 0.f) * 0.63661977f, 1.f) * 1048575.f);
+}
+
 template <bool F64>
 __global__ void __launch_bounds__(128) shepard_kernel(SupportArgs a, double rho_aux2) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -497,6 +504,8 @@ __global__ void __launch_bounds__(128) shepard_kernel(SupportArgs a, double rho_
         a.deltaf[j] = (float)delta;
         a.rho2f[j] = (float)rho2;
         a.guarded[j] = 0;
+        a.order_keys[j] = order_key((float)delta);
+        a.order_vals[j] = (uint32_t)j;
       }
     } else {
       // MIXED: the support radius in FP32 throughout
@@ -528,6 +537,8 @@ __global__ void __launch_bounds__(128) shepard_kernel(SupportArgs a, double rho_
         a.delta[j] = (double)delta;
         a.rho2[j] = (double)rho2;
         a.guarded[j] = 0;
+        a.order_keys[j] = order_key(delta);
+        a.order_vals[j] = (uint32_t)j;
       }
     }
   }
@@ -559,26 +570,6 @@ __device__ __forceinline__ uint32_t ball_count(const Cells& g, float qxf, float 
   return warp_sum(cnt);
 }
 
-__global__ void __launch_bounds__(128) count_kernel(SupportArgs a) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const int L = 2 * a.N + 2, MQ = (a.N + 1) * L;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int j = warp; j < MQ; j += nw) {
-    const int k = j / L, jj = j - k * L;
-    const double qx = a.ring_s[k] * a.cphi[jj], qy = a.ring_s[k] * a.sphi[jj], qz = a.ring_t[k];
-    const float qxf = a.sf[k] * a.cpf[jj], qyf = a.sf[k] * a.spf[jj], qzf = a.tf[k];
-    uint32_t cnt = ball_count(a.nodes, qxf, qyf, qzf, qx, qy, qz, a.deltaf[j], a.rho2[j]);
-    if (lane == 0) {
-      a.count[j] = (int32_t)cnt;
-      if ((int)cnt < a.m) {
-        unsigned long long pos = atomicAdd(&a.st->cnt[C_GUARD_LIST], 1ull);
-        a.guard_list[pos] = (uint32_t)j;
-      }
-    }
-  }
-}
-
 // guard: delta = (1 + eps) d_n(q) computed exactly at q (Sec. 2.2 notes that
 // the smoothed radius holds at least n nodes only for a fine enough auxiliary
 // grid; this restores #X(q) >= m where it does not)
@@ -589,7 +580,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) guard_kernel(SupportArgs a, do
   const int nw = gridDim.x * KNN_WARPS;
   const int total = (int)a.st->cnt[C_GUARD_LIST];
   for (int e = blockIdx.x * KNN_WARPS + warp; e < total; e += nw) {
-    const int j = (int)a.guard_list[e];
+    const int j = (int)a.order[a.guard_list[e]];
     const int k = j / L, jj = j - k * L;
     const double qx = a.ring_s[k] * a.cphi[jj], qy = a.ring_s[k] * a.sphi[jj], qz = a.ring_t[k];
     bool failed = false;
@@ -611,34 +602,11 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) guard_kernel(SupportArgs a, do
       a.rho2f[j] = (float)rho2;
       a.count[j] = (int32_t)cnt;
       a.guarded[j] = 1;
+      atomicAdd(&a.st->cnt[C_SUM_N], (unsigned long long)cnt);
+      atomicAdd(&a.st->cnt[C_GUARD], 1ull);
+      atomicMin(&a.st->cnt[C_MIN_N], (unsigned long long)cnt);
+      atomicMax(&a.st->cnt[C_MAX_N], (unsigned long long)cnt);
     }
-  }
-}
-
-// cost keys for the MLS work order (heaviest first) and n(q) statistics
-__global__ void order_keys_kernel(SupportArgs a, int MQ) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned long long c = 0, mn = ~0ull, mx = 0, g = 0;
-  if (j < MQ) {
-    int cnt = a.count[j];
-    c = (unsigned long long)cnt;
-    mn = mx = c;
-    g = a.guarded[j];
-    a.order_keys[j] = 0xFFFFFu - (uint32_t)min(cnt, 0xFFFFF);
-    a.order_vals[j] = (uint32_t)j;
-  }
-  c = warp_sum(c);
-  g = warp_sum(g);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    mn = min(mn, __shfl_xor_sync(FULL, mn, o));
-    mx = max(mx, __shfl_xor_sync(FULL, mx, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&a.st->cnt[C_SUM_N], c);
-    atomicAdd(&a.st->cnt[C_GUARD], g);
-    atomicMin(&a.st->cnt[C_MIN_N], mn);
-    atomicMax(&a.st->cnt[C_MAX_N], mx);
   }
 }
 
@@ -680,12 +648,9 @@ void run_shepard(const SupportArgs& a, cudaStream_t s, int64_t* launches) {
   ++*launches;
 }
 
-void run_counts(const SupportArgs& a, cudaStream_t s, int64_t* launches) {
-  const int MQ = (a.N + 1) * (2 * a.N + 2);
-  count_kernel<<<grid_for(MQ, 4, 148 * 16), 128, 0, s>>>(a);
-  guard_kernel<<<148 * 2, KNN_WARPS * 32, 0, s>>>(a, initial_radius(a.n_target, a.nodes.n));
-  order_keys_kernel<<<(MQ + 255) / 256, 256, 0, s>>>(a, MQ);
-  *launches += 3;
+void run_guard(const SupportArgs& a, cudaStream_t s, int64_t* launches) {
+  guard_kernel<<<a.num_sms * 2, KNN_WARPS * 32, 0, s>>>(a, initial_radius(a.n_target, a.nodes.n));
+  ++*launches;
 }
 
 void run_knn_queries(const Cells& nodes, const double* q, int64_t nq, int n, double* c2_out, DevStatus* st,

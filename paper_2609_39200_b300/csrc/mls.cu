@@ -249,7 +249,11 @@ __device__ __forceinline__ void reduce_scatter64(const T (&acc)[NV], T& out0, T&
 // the work order are handed out one at a time, the rest in chunks of 16). The
 // warp streams the node's candidates, accumulates the moments and writes them
 // to mom[position * NVP + i] for the solve kernel.
-template <int K, bool MIXED>
+//
+// The gather also counts n(q) = #X(q) (eq. number_of_local_nodes) and lists
+// the positions with n(q) < m for the guard. LIST = true gathers only the
+// listed positions again, after the guard has widened their supports.
+template <int K, bool MIXED, bool LIST>
 __global__ void __launch_bounds__(MLS_WARPS * 32) mls_gather_kernel(MlsArgs a, unsigned long long* ctr,
                                                                     long long heavy) {
   using T = typename std::conditional<MIXED, float, double>::type;
@@ -257,22 +261,26 @@ __global__ void __launch_bounds__(MLS_WARPS * 32) mls_gather_kernel(MlsArgs a, u
   const int lane = threadIdx.x & 31;
   const int L = 2 * a.N + 2;
   T* mom = reinterpret_cast<T*>(a.mom);
+  const long long items = LIST ? (long long)a.st->cnt[C_GUARD_LIST] : (long long)a.MQ;
+  unsigned long long s_n = 0, s_min = ~0ull, s_max = 0, s_guarded = 0;   // lane 0's tallies
   for (;;) {
     unsigned long long c = 0;
     if (lane == 0) c = atomicAdd(ctr, 1ull);
     c = __shfl_sync(FULL, c, 0);
     long long p0, p1;
-    if ((long long)c < heavy) {
+    if (LIST || (long long)c < heavy) {
       p0 = (long long)c;
       p1 = p0 + 1;
     } else {
       p0 = heavy + ((long long)c - heavy) * 16;
       p1 = p0 + 16;
     }
-    if (p0 >= a.MQ) break;
-    if (p1 > a.MQ) p1 = a.MQ;
-    for (long long pos = p0; pos < p1; ++pos) {
+    if (p0 >= items) break;
+    if (p1 > items) p1 = items;
+    for (long long it = p0; it < p1; ++it) {
+      const long long pos = LIST ? (long long)a.guard_list[it] : it;
       const int j = (int)a.order[pos];
+      uint32_t nin = 0;
       const int k = j / L, jj = j - k * L;
       T acc[NV];
 #pragma unroll
@@ -291,6 +299,7 @@ __global__ void __launch_bounds__(MLS_WARPS * 32) mls_gather_kernel(MlsArgs a, u
           const float dx = p.x - qxf, dy = p.y - qyf, dz = p.z - qzf;
           const float c2 = dx * dx + dy * dy + dz * dz;
           if (!(c2 < r2f)) return;
+          ++nin;
           float w = wendland(geodesic_from_chord2(c2) * idf);
           if (a.swf) w *= a.swf[idx];
           const float u = e1x * dx + e1y * dy + e1z * dz;
@@ -316,6 +325,7 @@ __global__ void __launch_bounds__(MLS_WARPS * 32) mls_gather_kernel(MlsArgs a, u
           const double X = a.nodes.px[idx], Y = a.nodes.py[idx], Z = a.nodes.pz[idx];
           const double c2 = chord2_exact(X, Y, Z, qx, qy, qz);
           if (!(c2 < rho2)) return;
+          ++nin;
           const double dx = X - qx, dy = Y - qy, dz = Z - qz;
           double w = wendland(geodesic_from_chord2(c2) * id);
           if (a.sw) w *= a.sw[idx];
@@ -329,7 +339,28 @@ __global__ void __launch_bounds__(MLS_WARPS * 32) mls_gather_kernel(MlsArgs a, u
       T* dst = mom + pos * NVP;
       if (2 * lane < NV) dst[2 * lane] = o0;
       if (2 * lane + 1 < NV) dst[2 * lane + 1] = o1;
+      if (!LIST) {
+        nin = warp_sum(nin);
+        if (lane == 0) {
+          a.count[j] = (int32_t)nin;
+          if ((int)nin < a.m) {
+            const unsigned long long e = atomicAdd(&a.st->cnt[C_GUARD_LIST], 1ull);
+            a.guard_list[e] = (uint32_t)pos;
+          } else {
+            s_n += nin;
+            s_min = min(s_min, (unsigned long long)nin);
+            s_max = max(s_max, (unsigned long long)nin);
+            s_guarded += a.guarded[j];
+          }
+        }
+      }
     }
+  }
+  if (!LIST && lane == 0) {
+    atomicAdd(&a.st->cnt[C_SUM_N], s_n);
+    atomicAdd(&a.st->cnt[C_GUARD], s_guarded);
+    atomicMin(&a.st->cnt[C_MIN_N], s_min);
+    atomicMax(&a.st->cnt[C_MAX_N], s_max);
   }
 }
 
@@ -409,12 +440,18 @@ __global__ void __launch_bounds__(128) redo_kernel(MlsArgs a, SolveParams P) {
 
 template <int K, bool MIXED>
 static void launch_mls(const MlsArgs& a, const SolveParams& P, unsigned long long* ctr, cudaStream_t s,
-                       int64_t* launches) {
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mls_gather_kernel<K, MIXED>, MLS_WARPS * 32, 0);
-  if (per_sm < 1) per_sm = 1;
-  const long long heavy = a.MQ < 4096 ? a.MQ : (a.MQ / 8 > 4096 ? a.MQ / 8 : 4096);
-  mls_gather_kernel<K, MIXED><<<per_sm * a.num_sms, MLS_WARPS * 32, 0, s>>>(a, ctr, heavy);
+                       int64_t* launches, int part) {
+  if (part == 1) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mls_gather_kernel<K, MIXED, false>, MLS_WARPS * 32, 0);
+    if (per_sm < 1) per_sm = 1;
+    const long long heavy = a.MQ < 4096 ? a.MQ : (a.MQ / 8 > 4096 ? a.MQ / 8 : 4096);
+    mls_gather_kernel<K, MIXED, false><<<per_sm * a.num_sms, MLS_WARPS * 32, 0, s>>>(a, ctr, heavy);
+    ++*launches;
+    return;
+  }
+  // the listed positions (usually none) gathered again with their guarded radii
+  mls_gather_kernel<K, MIXED, true><<<a.num_sms, MLS_WARPS * 32, 0, s>>>(a, &a.st->cnt[C_LIST_BATCH], 0);
   mls_solve_kernel<K, MIXED><<<(a.MQ + 127) / 128, 128, 0, s>>>(a, P);
   *launches += 2;
   if (MIXED) {
@@ -423,7 +460,7 @@ static void launch_mls(const MlsArgs& a, const SolveParams& P, unsigned long lon
   }
 }
 
-void run_mls(const MlsArgs& a, bool mixed, cudaStream_t s, int64_t* launches) {
+void run_mls(const MlsArgs& a, bool mixed, cudaStream_t s, int64_t* launches, int part) {
   SolveParams P;
   P.chiT = a.chiT;
   P.chiF = a.chiF;
@@ -431,14 +468,14 @@ void run_mls(const MlsArgs& a, bool mixed, cudaStream_t s, int64_t* launches) {
   for (int l = 0; l <= KMAX; ++l) P.mu[l] = a.mu[l];
   unsigned long long* ctr = &a.st->cnt[C_BATCH];
   switch (a.K * 2 + (mixed ? 1 : 0)) {
-    case 2: launch_mls<1, false>(a, P, ctr, s, launches); break;
-    case 3: launch_mls<1, true>(a, P, ctr, s, launches); break;
-    case 4: launch_mls<2, false>(a, P, ctr, s, launches); break;
-    case 5: launch_mls<2, true>(a, P, ctr, s, launches); break;
-    case 6: launch_mls<3, false>(a, P, ctr, s, launches); break;
-    case 7: launch_mls<3, true>(a, P, ctr, s, launches); break;
-    case 8: launch_mls<4, false>(a, P, ctr, s, launches); break;
-    case 9: launch_mls<4, true>(a, P, ctr, s, launches); break;
+    case 2: launch_mls<1, false>(a, P, ctr, s, launches, part); break;
+    case 3: launch_mls<1, true>(a, P, ctr, s, launches, part); break;
+    case 4: launch_mls<2, false>(a, P, ctr, s, launches, part); break;
+    case 5: launch_mls<2, true>(a, P, ctr, s, launches, part); break;
+    case 6: launch_mls<3, false>(a, P, ctr, s, launches, part); break;
+    case 7: launch_mls<3, true>(a, P, ctr, s, launches, part); break;
+    case 8: launch_mls<4, false>(a, P, ctr, s, launches, part); break;
+    case 9: launch_mls<4, true>(a, P, ctr, s, launches, part); break;
     default: break;
   }
 }
