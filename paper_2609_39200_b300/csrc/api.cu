@@ -338,7 +338,7 @@ hamls_status build_nodes(hamls_plan_s* P, const double* nodes, const double* wts
   run_shepard(a, s, &P->launches);
   stage_end(P, 2, s);
   stage_begin(P, 3, s);
-  bool alt = radix_sort_pairs(P->okeys, P->ovals, P->okeys_alt, P->ovals_alt, P->MQ, 20, P->counts, s,
+  bool alt = radix_sort_pairs(P->okeys, P->ovals, P->okeys_alt, P->ovals_alt, P->MQ, 3, P->counts, s,
                               &P->launches);
   P->order = alt ? P->ovals_alt : P->ovals;
   stage_end(P, 3, s);

@@ -25,7 +25,9 @@ __global__ void keys_kernel(const double* __restrict__ xyz, int n, int B, int P,
     set_flag(st, ST_BADNODE);
     x = 0.0; y = 0.0; z = 1.0;
   }
-  keys[i] = cell_key64(x, y, z, B, P);
+  uint32_t key;
+  if (!cell_key_fast(x, y, z, B, P, key)) key = cell_key64(x, y, z, B, P);
+  keys[i] = key;
   idx[i] = (uint32_t)i;
 }
 

@@ -89,6 +89,36 @@ __device__ __forceinline__ uint32_t cell_key64(double x, double y, double z, int
   return (uint32_t)(band * P + q * qc + w);
 }
 
+// The same key from FP32 arithmetic where that is provably the same: false
+// when a band or cell coordinate lies within 2e-3 of an integer (the FP32
+// error there is below 7e-4 for B/2, P/4 <= 2048), and the caller then takes
+// cell_key64. 1 - |z| is formed in FP64 so that the polar cancellation is exact.
+__device__ __forceinline__ bool cell_key_fast(double x, double y, double z, int B, int P, uint32_t& key) {
+  const float t = (float)__dsub_rn(1.0, fabs(z));
+  const float om = 1.f - sqrtf(t);
+  const float zeta = z < 0 ? -om : om;
+  const float bf = (zeta + 1.f) * (float)(B / 2);
+  const float fb = floorf(bf);
+  if (!(bf - fb > 2e-3f && bf - fb < 1.f - 2e-3f)) return false;
+  int q;
+  double num;
+  if (x > 0 && y >= 0) { q = 0; num = fabs(y); }
+  else if (x <= 0 && y > 0) { q = 1; num = fabs(x); }
+  else if (x < 0 && y <= 0) { q = 2; num = fabs(y); }
+  else if (x >= 0 && y < 0) { q = 3; num = fabs(x); }
+  else return false;
+  const float den = (float)fabs(x) + (float)fabs(y);
+  if (!(den > 1e-30f)) return false;
+  const int qc = P / 4;
+  const float cf = ((float)num / den) * (float)qc;
+  const float fc = floorf(cf);
+  if (!(cf - fc > 2e-3f && cf - fc < 1.f - 2e-3f)) return false;
+  const int band = min(max((int)fb, 0), B - 1);
+  const int w = min(max((int)fc, 0), qc - 1);
+  key = (uint32_t)(band * P + q * qc + w);
+  return true;
+}
+
 // FP32 versions used only to enumerate candidates (with margins).
 __device__ __forceinline__ int band_of_f(float z, int B) {
   float s = sqrtf(fmaxf(0.f, 1.f - fabsf(z)));

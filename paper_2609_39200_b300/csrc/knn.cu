@@ -453,11 +453,14 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_query_kernel(Cells nodes, 
 }
 
 // --------------------------------------------------------- Shepard / delta
-// Work-order key of a grid node, heaviest first: the support radius stands in
-// for the node's cost (large radii sit in holes of the node set, where a cap
-// collects its nodes from a long rim).
-__device__ __forceinline__ uint32_t order_key(float delta) {
-  return 0xFFFFFu - (uint32_t)(fminf(fmaxf(delta, 0.f) * 0.63661977f, 1.f) * 1048575.f);
+// Work-order key of a grid node, heaviest first: the support radius, in
+// octaves of the uniform-density radius d_typ = 2 sqrt(n/M), stands in for
+// the node's cost (large radii sit in holes of the node set, where a cap
+// collects its nodes from a long rim). Within a class the stable sort keeps
+// the grid order, so consecutive work shares cached nodes.
+__device__ __forceinline__ uint32_t order_key(float delta, float dtyp) {
+  const float c = fminf(fmaxf(log2f(fmaxf(delta, 1e-30f) / dtyp), 0.f), 7.f);
+  return 7u - (uint32_t)c;
 }
 
 template <bool F64>
@@ -467,6 +470,7 @@ __global__ void __launch_bounds__(128) shepard_kernel(SupportArgs a, double rho_
   const int L = 2 * a.N + 2, MQ = (a.N + 1) * L;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const float rho_f = (float)a.rho_aux, r2_f = (float)rho_aux2, irho_f = 1.f / rho_f;
+  const float dtyp = 2.f * sqrtf((float)a.n_target / (float)a.nodes.n);
   for (int j = warp; j < MQ; j += nw) {
     const int k = j / L, jj = j - k * L;
     const float qxf = a.sf[k] * a.cpf[jj], qyf = a.sf[k] * a.spf[jj], qzf = a.tf[k];
@@ -504,7 +508,7 @@ __global__ void __launch_bounds__(128) shepard_kernel(SupportArgs a, double rho_
         a.deltaf[j] = (float)delta;
         a.rho2f[j] = (float)rho2;
         a.guarded[j] = 0;
-        a.order_keys[j] = order_key((float)delta);
+        a.order_keys[j] = order_key((float)delta, dtyp);
         a.order_vals[j] = (uint32_t)j;
       }
     } else {
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(128) shepard_kernel(SupportArgs a, double rho_
         a.delta[j] = (double)delta;
         a.rho2[j] = (double)rho2;
         a.guarded[j] = 0;
-        a.order_keys[j] = order_key(delta);
+        a.order_keys[j] = order_key(delta, dtyp);
         a.order_vals[j] = (uint32_t)j;
       }
     }

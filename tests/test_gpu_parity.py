@@ -72,6 +72,44 @@ def test_cell_keys_sort_and_runs_bit_exact(h, M, seed):
     assert np.array_equal(start.cpu().numpy().astype(np.int64), ostart)
 
 
+def _edge_points(B, P, k, seed):
+    """Unit vectors on and next to band edges (zeta = -1 + 2b/B) and cell
+    edges (|y|/(|x|+|y|) = w/(P/4)), where the key's integer part is decided
+    by the last bits of the FP64 arithmetic."""
+    rng = np.random.default_rng(seed)
+    # a third of the edges moved by 0.0021..0.01 of a band or cell: just
+    # outside the FP32 fast path's guard band, where that path must agree
+    near = np.where(rng.random(k) < 1 / 3, rng.choice([-1.0, 1.0], k) * rng.uniform(0.0021, 0.01, k), 0.0)
+    b = rng.integers(1, B, k)
+    zeta = -1.0 + 2.0 * (b + near) / B
+    z = np.where(zeta >= 0, 1.0 - (1.0 - zeta) ** 2, (1.0 + zeta) ** 2 - 1.0)
+    z = z + rng.choice([-1.0, 0.0, 1.0], k) * np.spacing(np.abs(z) + 1e-300) * rng.integers(0, 3, k)
+    qc = P // 4
+    w = np.clip(rng.integers(0, qc + 1, k) + near, 0, qc)
+    ay, ax = w / qc, 1.0 - w / qc
+    sx, sy = rng.choice([-1.0, 1.0], k), rng.choice([-1.0, 1.0], k)
+    rho = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    nrm = np.hypot(ax, ay)
+    x = np.stack([sx * ax / nrm * rho, sy * ay / nrm * rho, z], axis=1)
+    # half of them with only the band edge, at a random longitude
+    phi = rng.uniform(0, 2 * np.pi, k)
+    half = rng.random(k) < 0.5
+    x[half, 0], x[half, 1] = rho[half] * np.cos(phi[half]), rho[half] * np.sin(phi[half])
+    return x / np.linalg.norm(x, axis=1, keepdims=True)
+
+
+def test_cell_keys_on_edges_bit_exact(h):
+    # 20000 nodes give 128 bands of 256 cells
+    x = _edge_points(128, 256, 20000, 9)
+    with h.Plan(dev(x), 8, 2) as p:
+        keys, perm, start, B, P = p.debug_cells()
+        p.sync(60000)
+    assert (B, P) == (128, 256)
+    operm, sk, ostart = O.cell_sort(O.cell_keys(x, B, P), B * P)
+    assert np.array_equal(keys.cpu().numpy().astype(np.int64), sk)
+    assert np.array_equal(perm.cpu().numpy().astype(np.int64), operm)
+
+
 @pytest.mark.parametrize("n", [1, 6, 24, 40, 128])
 def test_knn_bit_exact(h, n):
     x, _ = __import__("hamls_synth").track_hole_nodes(11, 30000)
