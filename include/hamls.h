@@ -113,6 +113,9 @@ void hamls_default_params(hamls_params* p);
  *   K            MLS degree, 1 <= K <= 4
  *   p            parameters, NULL for the defaults
  *   stream       CUDA stream for all work (0 = legacy default stream)
+ * The smoothing of d_n onto the grid (Shepard, Sec. 2.2) uses a fixed radius
+ * on fixed grids, so the plan stores it as a sparse operator; to size that
+ * operator hamls_plan waits once for its stream. Later work stays asynchronous.
  * Returns HAMLS_OK, HAMLS_ERR_INVALID_ARG, HAMLS_ERR_OOM or HAMLS_ERR_CUDA.
  */
 hamls_status hamls_plan(hamls_plan_t* out, const double* nodes_xyz, const double* node_weights,

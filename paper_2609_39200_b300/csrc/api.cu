@@ -95,6 +95,12 @@ struct hamls_plan_s {
   float4* apf;
   uint32_t *tkeys, *tvals, *tkeys_alt, *tvals_alt;
   const uint32_t* tile_order = nullptr;
+  // Shepard operator: CSR start in the arena; columns, weights and weight
+  // sums in one allocation sized at plan time
+  uint32_t* shep_start;
+  void* shep_mem = nullptr;
+  uint32_t* shep_col = nullptr;
+  void *shep_w = nullptr, *shep_sw = nullptr;
   // grid nodes
   double *delta, *rho2, *fgrid, *chi, *tau;
   float *deltaf, *rho2f;
@@ -190,6 +196,7 @@ void carve(hamls_plan_s* P) {
   P->tvals = A.take<uint32_t>(Ma);
   P->tkeys_alt = A.take<uint32_t>(Ma);
   P->tvals_alt = A.take<uint32_t>(Ma);
+  P->shep_start = A.take<uint32_t>((size_t)MQ + 1);
   // grid nodes
   P->delta = A.take<double>(MQ);
   P->rho2 = A.take<double>(MQ);
@@ -284,6 +291,10 @@ SupportArgs support_args(hamls_plan_s* P) {
   a.order = P->order;
   a.fp64 = P->mixed ? 0 : 1;
   a.tile_order = P->tile_order;
+  a.shep_start = P->shep_start;
+  a.shep_col = P->shep_col;
+  a.shep_w = P->shep_w;
+  a.shep_sw = P->shep_sw;
   a.num_sms = P->num_sms;
   a.st = P->st;
   return a;
@@ -379,6 +390,21 @@ hamls_status build_static(hamls_plan_s* P, cudaStream_t s) {
   bt = bt < 2 ? 2 : (bt > 4096 ? 4096 : bt);
   build_tile_order(P->apx, P->apy, P->apz, P->M_aux, bt, 8192, P->tkeys, P->tvals, P->tkeys_alt, P->tvals_alt,
                    P->counts, &P->tile_order, s, &P->launches);
+  // the Shepard operator: count members per grid node, scan, size, fill
+  shepard_rows(support_args(P), P->shep_start, nullptr, nullptr, nullptr, false, s, &P->launches);
+  HAMLS_TRY(cudaMemsetAsync(P->shep_start + P->MQ, 0, sizeof(uint32_t), s));
+  exclusive_scan_u32(P->shep_start, P->MQ + 1, P->counts, s, &P->launches);
+  uint32_t nnz = 0;
+  HAMLS_TRY(cudaMemcpyAsync(&nnz, P->shep_start + P->MQ, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  HAMLS_TRY(cudaStreamSynchronize(s));
+  const size_t wsz = P->mixed ? sizeof(float) : sizeof(double);
+  auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t b_col = up((size_t)nnz * 4 + 4), b_w = up((size_t)nnz * wsz + wsz), b_sw = up((size_t)P->MQ * wsz);
+  HAMLS_TRY(cudaMalloc(&P->shep_mem, b_col + b_w + b_sw));
+  P->shep_col = reinterpret_cast<uint32_t*>(P->shep_mem);
+  P->shep_w = reinterpret_cast<char*>(P->shep_mem) + b_col;
+  P->shep_sw = reinterpret_cast<char*>(P->shep_mem) + b_col + b_w;
+  shepard_rows(support_args(P), P->shep_start, P->shep_col, P->shep_w, P->shep_sw, true, s, &P->launches);
   return cuda_status(cudaGetLastError());
 }
 
@@ -637,6 +663,7 @@ hamls_status hamls_destroy(hamls_plan_t P) {
       cudaEventDestroy(P->ev[i][1]);
     }
   if (P->arena.base) cudaFree(P->arena.base);
+  if (P->shep_mem) cudaFree(P->shep_mem);
   if (P->st_host) cudaFreeHost(P->st_host);
   delete P;
   return HAMLS_OK;

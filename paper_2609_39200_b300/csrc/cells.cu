@@ -179,6 +179,14 @@ __global__ void __launch_bounds__(SORT_THREADS) radix_scatter(const uint32_t* __
   }
 }
 
+void exclusive_scan_u32(uint32_t* a, int len, uint32_t* part, cudaStream_t s, int64_t* launches) {
+  const int nt = (len + SCAN_TILE - 1) / SCAN_TILE;
+  scan_tile_sums<<<nt, 256, 0, s>>>(a, len, part);
+  scan_sums<<<1, 256, 0, s>>>(part, nt);
+  scan_tiles<<<nt, 256, 0, s>>>(a, len, part);
+  *launches += 3;
+}
+
 // Stable sort of (keys, vals) by the low `bits` key bits. Returns true when the
 // result ended in the *_alt buffers.
 bool radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int n, int bits,

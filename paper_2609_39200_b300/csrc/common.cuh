@@ -301,54 +301,90 @@ __device__ __forceinline__ void cap_band_range(const Cells& g, const Cap& c, int
   b_hi = min(band_of_f(c.zhi, g.B) + 1, g.B - 1);
 }
 
-// Warp-cooperative enumeration of every sorted point index that can lie in
-// the cap. The runs of 32 consecutive bands are concatenated and dealt to the
-// lanes 32 at a time, so consecutive lanes read consecutive points. f(valid,
-// idx) is called by all 32 lanes together (it may use warp intrinsics).
+// ---------------------------------------------------------- lane groups
+// A query can be served by a group of G consecutive lanes (G = 8, 16 or 32):
+// every shuffle below has width G, so the groups of a warp run the same
+// instructions side by side on their own queries. Loops run while any group
+// still has work (warp-wide votes keep the warp converged); a group without
+// work takes part with neutral values.
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o, G);
+  return v;
+}
+
+template <int G>
+__device__ __forceinline__ float group_max(float v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o, G));
+  return v;
+}
+
+// the group's lanes of a warp ballot, bit 0 = the group's first lane
+template <int G>
+__device__ __forceinline__ unsigned group_ballot(bool p) {
+  const unsigned b = __ballot_sync(FULL, p);
+  if (G == 32) return b;
+  return (b >> ((threadIdx.x & 31) & ~(G - 1))) & ((1u << (G & 31)) - 1u);
+}
+
+// Group-cooperative enumeration of every sorted point index that can lie in
+// the cap. The runs of G consecutive bands are concatenated and dealt to the
+// group's lanes G at a time, so consecutive lanes read consecutive points.
+// f(valid, idx) is called by all 32 lanes together; an inactive group (or a
+// lane past the end) gets valid = false.
 //
 // With MIDOUT the bands are visited from the cap centre's band outwards
 // (offsets 0, +1, -1, +2, -2, ...), so candidates arrive roughly nearest
 // first; searches that keep the n nearest then rarely update after a while.
-template <bool MIDOUT = false, class F>
-__device__ __forceinline__ void for_cap_candidates(const Cells& g, const Cap& c, F&& f) {
-  const int lane = threadIdx.x & 31;
+template <int G, bool MIDOUT = false, class F>
+__device__ __forceinline__ void for_cap_candidates_g(const Cells& g, const Cap& c, bool active, F&& f) {
+  const int gl = threadIdx.x & (G - 1);
   int b_lo, b_hi;
   cap_band_range(g, c, b_lo, b_hi);
   const int bc = MIDOUT ? min(max(band_of_f(c.zq, g.B), b_lo), b_hi) : b_lo;
-  const int span = MIDOUT ? 2 * max(bc - b_lo, b_hi - bc) + 1 : b_hi - b_lo + 1;
-  for (int k0 = 0; k0 < span; k0 += 32) {
-    const int k = k0 + lane;
+  int span = MIDOUT ? 2 * max(bc - b_lo, b_hi - bc) + 1 : b_hi - b_lo + 1;
+  if (!active) span = 0;
+  for (int k0 = 0; __any_sync(FULL, k0 < span); k0 += G) {
+    const int k = k0 + gl;
     const int b = MIDOUT ? bc + ((k & 1) ? (k + 1) / 2 : -(k / 2)) : b_lo + k;
     uint32_t s0 = 0, n0 = 0, s1 = 0, n1 = 0;
     if (k < span && b >= b_lo && b <= b_hi) band_runs(g, c, b, s0, n0, s1, n1);
     const uint32_t len = n0 + n1;
     uint32_t incl = len;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t t = __shfl_up_sync(FULL, incl, o);
-      if (lane >= o) incl += t;
+    for (int o = 1; o < G; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(FULL, incl, o, G);
+      if (gl >= o) incl += t;
     }
     const uint32_t excl = incl - len;
-    const uint32_t total = __shfl_sync(FULL, incl, 31);
-    for (uint32_t base = 0; base < total; base += 32) {
-      const uint32_t v = base + lane;
+    const uint32_t total = __shfl_sync(FULL, incl, G - 1, G);
+    for (uint32_t base = 0; __any_sync(FULL, base < total); base += G) {
+      const uint32_t v = base + gl;
       int owner = 0;
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        int cand = owner + step;
-        uint32_t e = __shfl_sync(FULL, excl, cand & 31);
-        if (cand < 32 && e <= v) owner = cand;
+      for (int step = G / 2; step > 0; step >>= 1) {
+        const int cand = owner + step;
+        const uint32_t e = __shfl_sync(FULL, excl, cand & (G - 1), G);
+        if (cand < G && e <= v) owner = cand;
       }
-      const uint32_t oe = __shfl_sync(FULL, excl, owner);
-      const uint32_t os0 = __shfl_sync(FULL, s0, owner);
-      const uint32_t on0 = __shfl_sync(FULL, n0, owner);
-      const uint32_t os1 = __shfl_sync(FULL, s1, owner);
+      const uint32_t oe = __shfl_sync(FULL, excl, owner, G);
+      const uint32_t os0 = __shfl_sync(FULL, s0, owner, G);
+      const uint32_t on0 = __shfl_sync(FULL, n0, owner, G);
+      const uint32_t os1 = __shfl_sync(FULL, s1, owner, G);
       const bool valid = v < total;
       const uint32_t off = v - oe;
       const uint32_t idx = valid ? ((off < on0) ? os0 + off : os1 + (off - on0)) : 0u;
       f(valid, idx);
     }
   }
+}
+
+// The warp-per-query enumeration (one group of 32 lanes).
+template <bool MIDOUT = false, class F>
+__device__ __forceinline__ void for_cap_candidates(const Cells& g, const Cap& c, F&& f) {
+  for_cap_candidates_g<32, MIDOUT>(g, c, true, f);
 }
 
 // Number of candidates the enumeration would visit (no point is read).

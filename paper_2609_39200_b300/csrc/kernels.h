@@ -26,6 +26,8 @@ void build_cells(const CellBuild& cb, cudaStream_t s, int64_t* launches);
 bool radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int n, int bits,
                       uint32_t* counts, cudaStream_t s, int64_t* launches);
 int scan_partials(int n);   // scratch words radix_sort_pairs needs after the counts (see cells.cu)
+// in-place exclusive scan of len words; part: (len + 1023) / 1024 + 1 words of scratch
+void exclusive_scan_u32(uint32_t* a, int len, uint32_t* part, cudaStream_t s, int64_t* launches);
 void launch_cell_keys(const double* xyz, int n, int B, int P, uint32_t* keys, uint32_t* vals, DevStatus* st,
                       cudaStream_t s);
 void launch_csr(const uint32_t* sk, int n, int ncells, uint32_t* start, cudaStream_t s);
@@ -73,10 +75,21 @@ struct SupportArgs {
   uint32_t* order_vals;         // M_Q
   int fp64;                     // 1: FP64 Shepard, 0: FP32
   const uint32_t* tile_order;   // aux points (sorted positions) in tile order
+  // the Shepard operator (CSR over grid nodes): auxiliary members of each
+  // grid node's cap, their Wendland weights (double FP64 / float MIXED) and
+  // the weight sums
+  const uint32_t* shep_start;
+  const uint32_t* shep_col;
+  const void* shep_w;
+  const void* shep_sw;
   int num_sms;
   DevStatus* st;
 };
 void run_aux_knn(const SupportArgs& a, cudaStream_t s, int64_t* launches);
+// plan time: members per grid node (fill = false, into rows) or the operator
+// itself (fill = true, rows = the CSR start array)
+void shepard_rows(const SupportArgs& a, uint32_t* rows, uint32_t* col, void* w, void* sw, bool fill,
+                  cudaStream_t s, int64_t* launches);
 void run_shepard(const SupportArgs& a, cudaStream_t s, int64_t* launches);
 // the guard of the listed work-order positions (Sec. 2.2): exact d_n at q
 void run_guard(const SupportArgs& a, cudaStream_t s, int64_t* launches);

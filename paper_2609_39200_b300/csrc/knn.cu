@@ -463,88 +463,127 @@ __device__ __forceinline__ uint32_t order_key(float delta, float dtyp) {
   return 7u - (uint32_t)c;
 }
 
-template <bool F64>
-__global__ void __launch_bounds__(128) shepard_kernel(SupportArgs a, double rho_aux2) {
+// The Shepard operator. The auxiliary grid, the quadrature grid and rho_aux
+// depend on the plan only, so the members of every grid node's Shepard cap
+// and their Wendland weights phi(d(q, a)/rho_aux) are found once, at plan
+// time, and each replan applies them to the new d_n:
+//   d~_n(q) = sum_a w_qa d_n(a) / sum_a w_qa.
+// FP64 form: exact membership and FP64 weights (FP32 only pre-filters);
+// MIXED: FP32 throughout. Members are stored in enumeration order.
+template <bool F64, bool FILL>
+__global__ void __launch_bounds__(128) shepard_rows_kernel(SupportArgs a, double rho_aux2, uint32_t* rows,
+                                                           uint32_t* col, void* wv, void* swv) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int L = 2 * a.N + 2, MQ = (a.N + 1) * L;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const float rho_f = (float)a.rho_aux, r2_f = (float)rho_aux2, irho_f = 1.f / rho_f;
-  const float dtyp = 2.f * sqrtf((float)a.n_target / (float)a.nodes.n);
+  const float hi_f = (float)(rho_aux2 + c2_margin(rho_aux2));
   for (int j = warp; j < MQ; j += nw) {
     const int k = j / L, jj = j - k * L;
     const float qxf = a.sf[k] * a.cpf[jj], qyf = a.sf[k] * a.spf[jj], qzf = a.tf[k];
-    Cap c = make_cap_f(qxf, qyf, qzf, rho_f);
-    if (F64) {
-      // FP64 form: exact membership and FP64 weights (FP32 only pre-filters)
-      const double qx = a.ring_s[k] * a.cphi[jj], qy = a.ring_s[k] * a.sphi[jj], qz = a.ring_t[k];
-      const float hi_f = (float)(rho_aux2 + c2_margin(rho_aux2));
-      double sw = 0.0, swd = 0.0;
-      for_cap_candidates(a.aux, c, [&](bool valid, uint32_t idx) {
-        if (!valid) return;
-        const float4 p = a.aux.pf[idx];
-        const float dx = p.x - qxf, dy = p.y - qyf, dz = p.z - qzf;
-        if (dx * dx + dy * dy + dz * dz > hi_f) return;
-        const double c2 = chord2_exact(a.aux.px[idx], a.aux.py[idx], a.aux.pz[idx], qx, qy, qz);
-        if (!(c2 < rho_aux2)) return;
-        const double w = wendland(geodesic_from_chord2(c2) / a.rho_aux);
-        sw += w;
-        swd += w * a.dn_aux_sorted[idx];
-      });
-      sw = warp_sum(sw);
-      swd = warp_sum(swd);
-      if (lane == 0) {
-        const double PI = 3.14159265358979323846;
-        double delta = (1.0 + a.eps) * (swd / sw);
-        if (!(sw > 0.0) || !(delta < 0.5 * PI)) {
-          set_flag(a.st, ST_SUPPORT);
-          delta = fmin(delta, 0.5 * PI);
-          if (!(delta > 0.0)) delta = 0.5 * PI;
-        }
-        const double sr = sin(0.5 * delta);
-        const double rho2 = 4.0 * sr * sr;
-        a.delta[j] = delta;
-        a.rho2[j] = rho2;
-        a.deltaf[j] = (float)delta;
-        a.rho2f[j] = (float)rho2;
-        a.guarded[j] = 0;
-        a.order_keys[j] = order_key((float)delta, dtyp);
-        a.order_vals[j] = (uint32_t)j;
-      }
-    } else {
-      // MIXED: the support radius in FP32 throughout
-      float sw = 0.f, swd = 0.f;
-      for_cap_candidates(a.aux, c, [&](bool valid, uint32_t idx) {
-        if (!valid) return;
+    const double qx = a.ring_s[k] * a.cphi[jj], qy = a.ring_s[k] * a.sphi[jj], qz = a.ring_t[k];
+    const Cap c = make_cap_f(qxf, qyf, qzf, rho_f);
+    uint32_t pos = FILL ? rows[j] : 0u;
+    double sw = 0.0;
+    float swf = 0.f;
+    for_cap_candidates(a.aux, c, [&](bool valid, uint32_t idx) {
+      bool in = false;
+      double w = 0.0;
+      float wf = 0.f;
+      if (valid) {
         const float4 p = a.aux.pf[idx];
         const float dx = p.x - qxf, dy = p.y - qyf, dz = p.z - qzf;
         const float c2f = dx * dx + dy * dy + dz * dz;
-        if (!(c2f < r2_f)) return;
-        const float w = wendland(geodesic_from_chord2(c2f) * irho_f);
-        sw += w;
-        swd += w * a.dn_aux_f[idx];
-      });
-      sw = warp_sum(sw);
-      swd = warp_sum(swd);
-      if (lane == 0) {
-        const float HPI = 1.57079632f;
-        float delta = (1.f + (float)a.eps) * (swd / sw);
-        if (!(sw > 0.f) || !(delta < HPI)) {
-          set_flag(a.st, ST_SUPPORT);
-          delta = fminf(delta, HPI);
-          if (!(delta > 0.f)) delta = HPI;
+        if (F64) {
+          if (c2f <= hi_f) {
+            const double c2 = chord2_exact(a.aux.px[idx], a.aux.py[idx], a.aux.pz[idx], qx, qy, qz);
+            in = c2 < rho_aux2;
+            if (in && FILL) w = wendland(geodesic_from_chord2(c2) / a.rho_aux);
+          }
+        } else {
+          in = c2f < r2_f;
+          if (in && FILL) wf = wendland(geodesic_from_chord2(c2f) * irho_f);
         }
-        const float sr = sinf(0.5f * delta);
-        const float rho2 = 4.f * sr * sr;
-        a.deltaf[j] = delta;
-        a.rho2f[j] = rho2;
-        a.delta[j] = (double)delta;
-        a.rho2[j] = (double)rho2;
-        a.guarded[j] = 0;
-        a.order_keys[j] = order_key(delta, dtyp);
-        a.order_vals[j] = (uint32_t)j;
       }
+      const unsigned b = __ballot_sync(FULL, in);
+      if (FILL && in) {
+        const uint32_t e = pos + __popc(b & ((1u << lane) - 1u));
+        col[e] = idx;
+        if (F64) {
+          reinterpret_cast<double*>(wv)[e] = w;
+          sw += w;
+        } else {
+          reinterpret_cast<float*>(wv)[e] = wf;
+          swf += wf;
+        }
+      }
+      pos += __popc(b);
+    });
+    if (FILL) {
+      if (F64) {
+        sw = warp_sum(sw);
+        if (lane == 0) reinterpret_cast<double*>(swv)[j] = sw;
+      } else {
+        swf = warp_sum(swf);
+        if (lane == 0) reinterpret_cast<float*>(swv)[j] = swf;
+      }
+    } else if (lane == 0) {
+      rows[j] = pos;
     }
+  }
+}
+
+// delta(q) = (1 + eps) d~_n(q) with the Shepard operator; one thread per grid
+// node (about 28 members each), summing its members in stored order. Also
+// resets the guard flag and writes the work-order key.
+template <bool F64>
+__global__ void __launch_bounds__(256) shepard_apply_kernel(SupportArgs a) {
+  using T = typename std::conditional<F64, double, float>::type;
+  const int MQ = (a.N + 1) * (2 * a.N + 2);
+  const T* w = reinterpret_cast<const T*>(a.shep_w);
+  const T* sws = reinterpret_cast<const T*>(a.shep_sw);
+  const T* dn = F64 ? reinterpret_cast<const T*>(a.dn_aux_sorted) : reinterpret_cast<const T*>(a.dn_aux_f);
+  const float dtyp = 2.f * sqrtf((float)a.n_target / (float)a.nodes.n);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < MQ; j += gridDim.x * blockDim.x) {
+    const uint32_t e0 = a.shep_start[j], e1 = a.shep_start[j + 1];
+    T swd = T(0);
+#pragma unroll 4
+    for (uint32_t e = e0; e < e1; ++e) swd += w[e] * dn[a.shep_col[e]];
+    const T sw = sws[j];
+    if (F64) {
+      const double PI = 3.14159265358979323846;
+      double delta = (1.0 + a.eps) * ((double)swd / (double)sw);
+      if (!(sw > 0) || !(delta < 0.5 * PI)) {
+        set_flag(a.st, ST_SUPPORT);
+        delta = fmin(delta, 0.5 * PI);
+        if (!(delta > 0.0)) delta = 0.5 * PI;
+      }
+      const double sr = sin(0.5 * delta);
+      const double rho2 = 4.0 * sr * sr;
+      a.delta[j] = delta;
+      a.rho2[j] = rho2;
+      a.deltaf[j] = (float)delta;
+      a.rho2f[j] = (float)rho2;
+      a.order_keys[j] = order_key((float)delta, dtyp);
+    } else {
+      const float HPI = 1.57079632f;
+      float delta = (1.f + (float)a.eps) * ((float)swd / (float)sw);
+      if (!(sw > 0) || !(delta < HPI)) {
+        set_flag(a.st, ST_SUPPORT);
+        delta = fminf(delta, HPI);
+        if (!(delta > 0.f)) delta = HPI;
+      }
+      const float sr = sinf(0.5f * delta);
+      const float rho2 = 4.f * sr * sr;
+      a.deltaf[j] = delta;
+      a.rho2f[j] = rho2;
+      a.delta[j] = (double)delta;
+      a.rho2[j] = (double)rho2;
+      a.order_keys[j] = order_key(delta, dtyp);
+    }
+    a.guarded[j] = 0;
+    a.order_vals[j] = (uint32_t)j;
   }
 }
 
@@ -640,15 +679,37 @@ void run_aux_knn(const SupportArgs& a, cudaStream_t s, int64_t* launches) {
   ++*launches;
 }
 
+static double aux_radius2(const SupportArgs& a) {
+  const double sr = sin(0.5 * a.rho_aux);
+  return 4.0 * sr * sr;
+}
+
+void shepard_rows(const SupportArgs& a, uint32_t* rows, uint32_t* col, void* w, void* sw, bool fill,
+                  cudaStream_t s, int64_t* launches) {
+  const int MQ = (a.N + 1) * (2 * a.N + 2);
+  const int blocks = grid_for(MQ, 4, 148 * 16);
+  const double r2 = aux_radius2(a);
+  if (a.fp64) {
+    if (fill)
+      shepard_rows_kernel<true, true><<<blocks, 128, 0, s>>>(a, r2, rows, col, w, sw);
+    else
+      shepard_rows_kernel<true, false><<<blocks, 128, 0, s>>>(a, r2, rows, col, w, sw);
+  } else {
+    if (fill)
+      shepard_rows_kernel<false, true><<<blocks, 128, 0, s>>>(a, r2, rows, col, w, sw);
+    else
+      shepard_rows_kernel<false, false><<<blocks, 128, 0, s>>>(a, r2, rows, col, w, sw);
+  }
+  ++*launches;
+}
+
 void run_shepard(const SupportArgs& a, cudaStream_t s, int64_t* launches) {
   const int MQ = (a.N + 1) * (2 * a.N + 2);
-  const double sr = sin(0.5 * a.rho_aux);
-  const double rho_aux2 = 4.0 * sr * sr;
-  const int blocks = grid_for(MQ, 4, 148 * 16);
+  const int blocks = (MQ + 255) / 256;
   if (a.fp64)
-    shepard_kernel<true><<<blocks, 128, 0, s>>>(a, rho_aux2);
+    shepard_apply_kernel<true><<<blocks, 256, 0, s>>>(a);
   else
-    shepard_kernel<false><<<blocks, 128, 0, s>>>(a, rho_aux2);
+    shepard_apply_kernel<false><<<blocks, 256, 0, s>>>(a);
   ++*launches;
 }
 
