@@ -127,8 +127,13 @@ __device__ __forceinline__ int band_of_f(float z, int B) {
   return min(max(b, 0), B - 1);
 }
 
-__device__ __forceinline__ int cell_of_f(float x, float y, int P) {
-  float ax = fabsf(x), ay = fabsf(y), den = ax + ay;
+
+// Continuous cell coordinate q P/4 + frac P/4 in [0, P] of a longitude: the
+// FP64 cell index of a point is its floor (clamped within the quadrant). It
+// is monotone and continuous in longitude, across quadrants too, so a run of
+// cells for an arc of longitudes is floor(lo - eps) .. floor(hi + eps).
+__device__ __forceinline__ float cell_coord_f(float x, float y, int P) {
+  const float ax = fabsf(x), ay = fabsf(y), den = ax + ay;
   int q;
   float num;
   if (x > 0.f && y >= 0.f) { q = 0; num = ay; }
@@ -136,11 +141,8 @@ __device__ __forceinline__ int cell_of_f(float x, float y, int P) {
   else if (x < 0.f && y <= 0.f) { q = 2; num = ay; }
   else if (x >= 0.f && y < 0.f) { q = 3; num = ax; }
   else { q = 0; num = 0.f; }
-  // approximate division: the runs built from this cell carry a one-cell margin
-  float frac = den > 0.f ? __fdividef(num, den) : 0.f;
-  int qc = P / 4;
-  int w = min(max((int)floorf(frac * (float)qc), 0), qc - 1);
-  return q * qc + w;
+  const float frac = den > 0.f ? __fdividef(num, den) : 0.f;
+  return ((float)q + frac) * (float)(P / 4);
 }
 
 __device__ __forceinline__ float zeta_to_z(float zeta) {
@@ -268,9 +270,10 @@ __device__ __forceinline__ void band_runs(const Cells& g, const Cap& c, int b, u
       const float sd = sqrtf(fmaxf(0.f, 1.f - cmin * cmin));
       const float xa = c.cph * cmin + c.sph * sd, ya = c.sph * cmin - c.cph * sd;   // phi_q - dphi
       const float xb = c.cph * cmin - c.sph * sd, yb = c.sph * cmin + c.cph * sd;   // phi_q + dphi
-      const int ca = cell_of_f(xa, ya, P), cb = cell_of_f(xb, yb, P);
-      int lo_c = ca - 1, hi_c = cb + 1;
-      if (ca > cb) hi_c += P;
+      // the FP32 coordinates are within 5e-4 cells of the exact ones (P <= 8192)
+      const float ga = cell_coord_f(xa, ya, P), gb = cell_coord_f(xb, yb, P);
+      int lo_c = (int)floorf(ga - 2e-3f), hi_c = (int)floorf(gb + 2e-3f);
+      if (ga > gb) hi_c += P;
       if (hi_c - lo_c + 1 >= P) {
         full = true;
       } else if (lo_c < 0) {
