@@ -237,13 +237,17 @@ __device__ int knn_select(const Cells& g, double qx, double qy, double qz, float
   }
   Cap c = make_cap_f(qxf, qyf, qzf, r);
   ++tally.scans;
+  // only points of the cap can be among the n nearest when it holds n of
+  // them; the bound is the widened radius's squared chord plus the FP32 error
+  const float rc2 = 4.f * c.rs * c.rs;                // squared chord of the widened radius
+  const float rcap2 = rc2 * (1.f + 1e-6f) + c2_margin_f(rc2) + 1e-12f;
   for_cap_candidates<true>(g, c, [&](bool valid, uint32_t idx) {
     if (!valid) return;
     ++tally.cand;
     const float4 p = g.pf[idx];
     const float dx = p.x - qxf, dy = p.y - qyf, dz = p.z - qzf;
     const float x = dx * dx + dy * dy + dz * dz;
-    if (x < key[KL - 1]) {
+    if (x < key[KL - 1] && x <= rcap2) {
       // insert after equal keys: every slot decides from the old list at once
       bool gt[KL];
 #pragma unroll
