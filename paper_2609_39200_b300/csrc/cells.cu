@@ -19,14 +19,22 @@ __global__ void keys_kernel(const double* __restrict__ xyz, int n, int B, int P,
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double x = xyz[3 * (size_t)i], y = xyz[3 * (size_t)i + 1], z = xyz[3 * (size_t)i + 2];
-  double r2 = x * x + y * y + z * z;
-  bool ok = isfinite(x) && isfinite(y) && isfinite(z) && fabs(r2 - 1.0) < 1e-6;
+  // unit-vector check in FP32 where it is certain (the FP32 |x|^2 is within
+  // 4e-7 of the exact one), in FP64 otherwise
+  const float xf = (float)x, yf = (float)y, zf = (float)z;
+  const float r2f = xf * xf + yf * yf + zf * zf;
+  bool ok = isfinite(r2f) && fabsf(r2f - 1.f) < 5e-7f;
   if (!ok) {
-    set_flag(st, ST_BADNODE);
-    x = 0.0; y = 0.0; z = 1.0;
+    const double r2 = x * x + y * y + z * z;
+    ok = isfinite(x) && isfinite(y) && isfinite(z) && fabs(r2 - 1.0) < 1e-6;
   }
   uint32_t key;
-  if (!cell_key_fast(x, y, z, B, P, key)) key = cell_key64(x, y, z, B, P);
+  if (!ok) {
+    set_flag(st, ST_BADNODE);
+    key = cell_key64(0.0, 0.0, 1.0, B, P);
+  } else if (!cell_key_fast(xf, yf, zf, (float)__dsub_rn(1.0, fabs(z)), B, P, key)) {
+    key = cell_key64(x, y, z, B, P);
+  }
   keys[i] = key;
   idx[i] = (uint32_t)i;
 }

@@ -91,26 +91,26 @@ __device__ __forceinline__ uint32_t cell_key64(double x, double y, double z, int
 
 // The same key from FP32 arithmetic where that is provably the same: false
 // when a band or cell coordinate lies within 2e-3 of an integer (the FP32
-// error there is below 7e-4 for B/2, P/4 <= 2048), and the caller then takes
-// cell_key64. 1 - |z| is formed in FP64 so that the polar cancellation is exact.
-__device__ __forceinline__ bool cell_key_fast(double x, double y, double z, int B, int P, uint32_t& key) {
-  const float t = (float)__dsub_rn(1.0, fabs(z));
+// error there is below 7e-4 for B/2, P/4 <= 2048) or when x or y rounds to
+// zero in FP32, and the caller then takes cell_key64. t = 1 - |z| comes
+// from FP64, so that the polar cancellation is exact; xf, yf, zf are x, y, z
+// rounded to FP32.
+__device__ __forceinline__ bool cell_key_fast(float xf, float yf, float zf, float t, int B, int P, uint32_t& key) {
+  if (xf == 0.f || yf == 0.f) return false;
   const float om = 1.f - sqrtf(t);
-  const float zeta = z < 0 ? -om : om;
+  const float zeta = zf < 0.f ? -om : om;
   const float bf = (zeta + 1.f) * (float)(B / 2);
   const float fb = floorf(bf);
   if (!(bf - fb > 2e-3f && bf - fb < 1.f - 2e-3f)) return false;
+  const float ax = fabsf(xf), ay = fabsf(yf);
   int q;
-  double num;
-  if (x > 0 && y >= 0) { q = 0; num = fabs(y); }
-  else if (x <= 0 && y > 0) { q = 1; num = fabs(x); }
-  else if (x < 0 && y <= 0) { q = 2; num = fabs(y); }
-  else if (x >= 0 && y < 0) { q = 3; num = fabs(x); }
-  else return false;
-  const float den = (float)fabs(x) + (float)fabs(y);
-  if (!(den > 1e-30f)) return false;
+  float num;
+  if (xf > 0.f && yf > 0.f) { q = 0; num = ay; }
+  else if (xf < 0.f && yf > 0.f) { q = 1; num = ax; }
+  else if (xf < 0.f) { q = 2; num = ay; }
+  else { q = 3; num = ax; }
   const int qc = P / 4;
-  const float cf = ((float)num / den) * (float)qc;
+  const float cf = (num / (ax + ay)) * (float)qc;
   const float fc = floorf(cf);
   if (!(cf - fc > 2e-3f && cf - fc < 1.f - 2e-3f)) return false;
   const int band = min(max((int)fb, 0), B - 1);
