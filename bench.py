@@ -32,7 +32,10 @@ WORKLOAD = "s2_n512_k3_m4m"
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each
 # stage's dominant kernel from an ncu capture (see profiles/); a stage whose
 # kernel changed after that capture has no entry and reports null.
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/aux_knn_kernel_s2_n512_k3_m4m.md: 193.9 MB read + 21.3 MB written
+    "aux_knn": 215_156_480,
+}
 
 
 def parse():
