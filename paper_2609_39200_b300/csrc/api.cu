@@ -82,6 +82,7 @@ struct hamls_plan_s {
   // scattered nodes
   int B = 0, P = 0;
   uint32_t *keys, *vals, *keys_alt, *vals_alt, *counts, *start;
+  float4 *edge, *aedge;            // band-edge tables of the node and auxiliary cells
   const uint32_t *perm = nullptr, *skeys = nullptr;
   double *px, *py, *pz, *sw, *sy;
   float4* pf;
@@ -170,6 +171,8 @@ void carve(hamls_plan_s* P) {
   P->vals_alt = A.take<uint32_t>(M);
   P->counts = A.take<uint32_t>((size_t)256 * radix_blocks(sortmax) + scan_partials(sortmax));
   P->start = A.take<uint32_t>((size_t)P->B * P->P + 1);
+  P->edge = A.take<float4>((size_t)P->B + 1);
+  P->aedge = A.take<float4>((size_t)P->aB + 1);
   P->px = A.take<double>(M);
   P->py = A.take<double>(M);
   P->pz = A.take<double>(M);
@@ -228,6 +231,7 @@ Cells node_cells(const hamls_plan_s* P) {
   c.P = P->P;
   c.n = (int)P->M;
   c.start = P->start;
+  c.edge = P->edge;
   c.pf = P->pf;
   c.px = P->px;
   c.py = P->py;
@@ -242,6 +246,7 @@ Cells aux_cells(const hamls_plan_s* P) {
   c.P = P->aP;
   c.n = P->M_aux;
   c.start = P->astart;
+  c.edge = P->aedge;
   c.pf = P->apf;
   c.px = P->apx;
   c.py = P->apy;
@@ -359,6 +364,8 @@ hamls_status build_nodes(hamls_plan_s* P, const double* nodes, const double* wts
 
 hamls_status build_static(hamls_plan_s* P, cudaStream_t s) {
   build_grid_tables(P->g, P->mixed, !P->mixed, s, &P->launches);
+  build_edge_table(P->B, P->edge, s, &P->launches);
+  build_edge_table(P->aB, P->aedge, s, &P->launches);
   fibonacci_points(P->ax, P->ay, P->az, P->M_aux, s, &P->launches);
   CellBuild cb;
   memset(&cb, 0, sizeof(cb));

@@ -187,6 +187,22 @@ __global__ void __launch_bounds__(SORT_THREADS) radix_scatter(const uint32_t* __
   }
 }
 
+// Half angles and z of every band edge (see Cells::edge).
+__global__ void edge_table_kernel(int B, float4* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e > B) return;
+  // 2/B exactly (B a power of two)
+  const float zstep = (B & (B - 1)) == 0 ? __int_as_float((128 - (__ffs(B) - 1)) << 23) : 2.f / (float)B;
+  float a, b;
+  edge_half_angles(-1.f + (float)e * zstep, a, b);
+  out[e] = make_float4(a, b, (b - a) * (b + a), 0.f);
+}
+
+void build_edge_table(int B, float4* out, cudaStream_t s, int64_t* launches) {
+  edge_table_kernel<<<(B + 1 + 255) / 256, 256, 0, s>>>(B, out);
+  ++*launches;
+}
+
 void exclusive_scan_u32(uint32_t* a, int len, uint32_t* part, cudaStream_t s, int64_t* launches) {
   const int nt = (len + SCAN_TILE - 1) / SCAN_TILE;
   scan_tile_sums<<<nt, 256, 0, s>>>(a, len, part);

@@ -52,6 +52,9 @@ struct Cells {
   const double* py;
   const double* pz;
   const uint32_t* perm;     // sorted position -> original index
+  // per band edge e = 0..B (zeta = -1 + 2e/B): sin and cos of half its
+  // colatitude and its z (edge_half_angles, tabulated once per plan)
+  const float4* edge;
 };
 
 // ---------------------------------------------------------------- warp utils
@@ -251,12 +254,9 @@ __device__ __forceinline__ void band_runs(const Cells& g, const Cap& c, int b, u
   n0 = n1 = 0;
   s0 = s1 = 0;
   const int B = g.B, P = g.P;
-  // band b spans zeta in [-1 + 2b/B, -1 + 2(b+1)/B); 2/B exactly (B a power of two)
-  const float zstep = (B & (B - 1)) == 0 ? __int_as_float((128 - (__ffs(B) - 1)) << 23) : 2.f / (float)B;
-  float ab, bb, at, bt;
-  edge_half_angles(-1.f + (float)b * zstep, ab, bb);
-  edge_half_angles(-1.f + (float)(b + 1) * zstep, at, bt);
-  const float z_bot = (bb - ab) * (bb + ab), z_top = (bt - at) * (bt + at);
+  // band b spans zeta in [-1 + 2b/B, -1 + 2(b+1)/B)
+  const float4 eb = g.edge[b], et = g.edge[b + 1];
+  const float ab = eb.x, bb = eb.y, z_bot = eb.z, at = et.x, bt = et.y, z_top = et.z;
   if (z_top < c.zlo || z_bot > c.zhi) return;               // band outside the cap's colatitudes
   const uint32_t base = (uint32_t)b * (uint32_t)P;
   bool full = c.polar;

@@ -26,6 +26,8 @@ void build_cells(const CellBuild& cb, cudaStream_t s, int64_t* launches);
 bool radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int n, int bits,
                       uint32_t* counts, cudaStream_t s, int64_t* launches);
 int scan_partials(int n);   // scratch words radix_sort_pairs needs after the counts (see cells.cu)
+// the band-edge table of a cell structure with B bands (B + 1 entries)
+void build_edge_table(int B, float4* out, cudaStream_t s, int64_t* launches);
 // in-place exclusive scan of len words; part: (len + 1023) / 1024 + 1 words of scratch
 void exclusive_scan_u32(uint32_t* a, int len, uint32_t* part, cudaStream_t s, int64_t* launches);
 void launch_cell_keys(const double* xyz, int n, int B, int P, uint32_t* keys, uint32_t* vals, DevStatus* st,
