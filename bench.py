@@ -41,7 +41,7 @@ TRAFFIC = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=3)
@@ -116,26 +116,66 @@ def run_reference(args):
 
 # -------------------------------------------------------------------- clocks
 class Clocks:
+    """SM clock and throttle reasons sampled during the timed region: NVML
+    polled every 10 ms from a thread (nvidia-smi at 50 ms if NVML is
+    unavailable). Samples go to gpurun_out/clocks_rank<i>.csv as well."""
+
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+               ("sw_power_cap", 0x4))
 
     def __init__(self, index: int):
         self.index = index
         self.p = None
+        self.thread = None
+        self.rows = []
+        self.nvml_error = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
 
+    def _poll(self, nv, h):
+        while not self.stop.is_set():
+            try:
+                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+                mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+                rs = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+                pw = nv.nvmlDeviceGetPowerUsage(h) / 1000.0
+                self.rows.append((sm, mx, rs, pw))
+            except Exception:
+                pass
+            self.stop.wait(0.01)
+
     def __enter__(self):
+        import threading
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            import pynvml as nv
+            nv.nvmlInit()
+            h = nv.nvmlDeviceGetHandleByIndex(self.index)
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._poll, args=(nv, h), daemon=True)
+            self.thread.start()
+            return self
+        except Exception as e:
+            self.thread = None
+            self.nvml_error = f"{type(e).__name__}: {e}"[:120]
+        try:
             self.fh = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv",
-                                       "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                                       "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.p = None
         return self
 
     def __exit__(self, *a):
+        if self.thread is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
+            with open(self.path, "w") as fh:
+                fh.write("sm_mhz,max_sm_mhz,event_reasons,power_w\n")
+                for r in self.rows:
+                    fh.write(f"{r[0]},{r[1]},{r[2]:#x},{r[3]:.1f}\n")
         if self.p is not None:
             self.p.terminate()
             try:
@@ -145,6 +185,12 @@ class Clocks:
             self.fh.close()
 
     def summary(self):
+        if self.thread is not None:
+            if not self.rows:
+                return None
+            reasons = sorted({n for r in self.rows for n, bit in self.REASONS if r[2] & bit})
+            return {"sm_mhz": float(np.median([r[0] for r in self.rows])), "sm_max_mhz": max(r[1] for r in self.rows),
+                    "reasons": reasons, "samples": len(self.rows), "source": "nvml, 10 ms"}
         if self.p is None or not os.path.exists(self.path):
             return None
         rows = [l.strip().split(", ") for l in open(self.path) if l.strip() and not l.startswith("index")]
@@ -154,7 +200,9 @@ class Clocks:
         mx = [float(r[2].split()[0]) for r in rows if len(r) > 2]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
-        return {"sm_mhz": float(np.median(mhz)), "sm_max_mhz": max(mx), "reasons": reasons, "samples": len(rows)}
+        return {"sm_mhz": float(np.median(mhz)), "sm_max_mhz": max(mx), "reasons": reasons, "samples": len(rows),
+                "source": "nvidia-smi, 50 ms", "nvml_error": self.nvml_error}
+
 
 
 # --------------------------------------------------------------------- ours

@@ -254,7 +254,9 @@ __device__ __forceinline__ void reduce_scatter64(const T (&acc)[NV], T& out0, T&
 // the positions with n(q) < m for the guard. LIST = true gathers only the
 // listed positions again, after the guard has widened their supports.
 template <int K, bool MIXED, bool LIST>
-__global__ void __launch_bounds__(MLS_WARPS * 32) mls_gather_kernel(MlsArgs a, unsigned long long* ctr,
+// 7 blocks of 4 warps per SM (at most 72 registers): more warps hide the
+// gather's L2 latency better than the registers they cost
+__global__ void __launch_bounds__(MLS_WARPS * 32, 7) mls_gather_kernel(MlsArgs a, unsigned long long* ctr,
                                                                     long long heavy) {
   using T = typename std::conditional<MIXED, float, double>::type;
   constexpr int NV = Shape<K>::NV, NVP = (NV + 1) & ~1;
