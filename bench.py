@@ -35,8 +35,10 @@ WORKLOAD = "s2_n512_k3_m4m"
 # stage's dominant kernel from an ncu capture (see profiles/); a stage whose
 # kernel changed after that capture has no entry and reports null.
 TRAFFIC = {
-    # profiles/aux_knn_kernel_s2_n512_k3_m4m.md: 193.9 MB read + 21.3 MB written
-    "aux_knn": 215_156_480,
+    # profiles/aux_knn_kernel_s2_n512_k3_m4m.md: 194.0 MB read + 21.3 MB written
+    "aux_knn": 215_310_080,
+    # profiles/mls_gather_kernel_s2_n512_k3_m4m.md (the MLS stage's main kernel): 80.6 + 50.4 MB
+    "mls": 131_017_472,
 }
 
 
@@ -405,7 +407,8 @@ def run_ours(args):
         if ms > 0:
             ach = nbytes / (ms / 1000.0) / 1e9
             stage_roof[st_name] = {"kernel": kname, "ms": round(ms, 4), "algorithmic_bytes": int(nbytes),
-                                   "achieved_gbs": round(ach, 1), "frac": round(ach / hbm_peak, 4)}
+                                   "achieved_gbs": round(ach, 1), "frac": round(ach / hbm_peak, 4),
+                                   "traffic": TRAFFIC.get(st_name)}
     dom = max(stages, key=lambda k: stages[k])
     dr = stage_roof.get(dom)
     roof = {"bound": "hbm", "kernel": dr["kernel"] if dr else dom, "achieved": dr["achieved_gbs"] if dr else None,
