@@ -141,6 +141,34 @@ hamls_status hamls_replan(hamls_plan_t plan, const double* nodes_xyz, const doub
  */
 hamls_status hamls_fit(hamls_plan_t plan, const double* values, double* coeffs, cudaStream_t stream);
 
+/*
+ * Values-only refits: new values at the same nodes (a time series on fixed
+ * stations). For fixed nodes every grid value f(q_j) = M_y(q_j) is linear in
+ * the data y: the Gram matrix, chi and tau~ of the local problem depend on the
+ * nodes only, and the data enter through the right-hand side (Sec. 2.3). The
+ * plan can therefore keep the fit as a sparse operator
+ *   f(q_j) = sum_{i in X(q_j)} A_ji y_i,
+ * and a refit is that product followed by step 3 (ring FFT, Legendre).
+ *
+ * hamls_refit_prepare - build the operator for the plan's current nodes: runs
+ *   the gather, the guard and the local solves once (n(q) statistics as for a
+ *   fit), then the entries. It allocates the operator's device memory (reused
+ *   by later calls when large enough; owned and freed by the plan): about
+ *   sum_q n(q) * 8 B (MIXED) or 12 B (FP64), plus M_Q * (4 + 4 (K+1)(K+2)) B
+ *   and 4 B per node of capacity,
+ *   and waits once for its stream to size it. hamls_replan invalidates the
+ *   operator. Returns HAMLS_ERR_CAPACITY beyond 2^32 - 1 entries, and
+ *   HAMLS_ERR_OOM or HAMLS_ERR_CUDA as hamls_plan.
+ * hamls_refit - coefficients for new values at the prepared nodes; arguments
+ *   as hamls_fit. HAMLS_ERR_INVALID_ARG if no operator exists for the current
+ *   nodes. FP64 plans reproduce hamls_fit up to rounding; MIXED plans store the
+ *   entries in FP32 (computed from the FP32 moments with FP64 local solves)
+ *   and sum their products with the FP32-rounded values in FP32. Non-finite
+ *   values are reported by hamls_sync.
+ */
+hamls_status hamls_refit_prepare(hamls_plan_t plan, cudaStream_t stream);
+hamls_status hamls_refit(hamls_plan_t plan, const double* values, double* coeffs, cudaStream_t stream);
+
 /* Wait (at most timeout_ms, < 0 = forever) for the plan's stream work and
  * return the first device-detected error, or HAMLS_OK. Clears the status. */
 hamls_status hamls_sync(hamls_plan_t plan, int timeout_ms);

@@ -60,6 +60,8 @@ _SIGS = {
     "hamls_plan": (_I, [ctypes.POINTER(_P), _P, _P, _I64, _I, _I, ctypes.POINTER(Params), _P]),
     "hamls_replan": (_I, [_P, _P, _P, _I64, _P]),
     "hamls_fit": (_I, [_P, _P, _P, _P]),
+    "hamls_refit_prepare": (_I, [_P, _P]),
+    "hamls_refit": (_I, [_P, _P, _P, _P]),
     "hamls_sync": (_I, [_P, _I]),
     "hamls_stats": (_I, [_P, ctypes.POINTER(FitStats)]),
     "hamls_destroy": (_I, [_P]),
@@ -165,6 +167,19 @@ class Plan:
             out = torch.empty((n_coeffs(self.N), 2), dtype=torch.float64, device=dev)
         self._keep_fit = (values, out)
         _check(lib().hamls_fit(self.h, _ptr(values), _ptr(out), _stream(stream)), "hamls_fit")
+        return out
+
+    def refit_prepare(self, stream=None):
+        """Keep the fit for the current nodes as a sparse operator of the values."""
+        _check(lib().hamls_refit_prepare(self.h, _stream(stream)), "hamls_refit_prepare")
+
+    def refit(self, values, out=None, stream=None):
+        """Coefficients for new values at the prepared nodes (same layout as fit)."""
+        if out is None:
+            dev = values.device if isinstance(values, torch.Tensor) and values.is_cuda else torch.device("cuda")
+            out = torch.empty((n_coeffs(self.N), 2), dtype=torch.float64, device=dev)
+        self._keep_refit = (values, out)
+        _check(lib().hamls_refit(self.h, _ptr(values), _ptr(out), _stream(stream)), "hamls_refit")
         return out
 
     def sync(self, timeout_ms: int = -1):

@@ -102,6 +102,16 @@ struct hamls_plan_s {
   void* shep_mem = nullptr;
   uint32_t* shep_col = nullptr;
   void *shep_w = nullptr, *shep_sw = nullptr;
+  // values-only refit operator (hamls_refit_prepare): CSR rows over grid
+  // nodes, original node indices, entries (float MIXED / double FP64), gamma
+  void* op_mem = nullptr;
+  size_t op_bytes = 0;
+  uint32_t *op_rows = nullptr, *op_col = nullptr;
+  void* op_val = nullptr;
+  double* op_gamma = nullptr;
+  float* op_yf = nullptr;          // MIXED: the values in FP32 for a refit
+  unsigned long long op_nnz = 0;
+  bool op_valid = false;
   // grid nodes
   double *delta, *rho2, *fgrid, *chi, *tau;
   float *deltaf, *rho2f;
@@ -308,6 +318,7 @@ SupportArgs support_args(hamls_plan_s* P) {
 // node-dependent part of the plan (Sec. 2.2: cell list, d_n, delta, n(q))
 hamls_status build_nodes(hamls_plan_s* P, const double* nodes, const double* wts, int64_t M, cudaStream_t s) {
   P->M = M;
+  P->op_valid = false;   // a refit operator belongs to the nodes it was built for
   P->has_weights = wts != nullptr;
   reset_status_kernel<<<1, 32, 0, s>>>(P->st, 1);
   ++P->launches;
@@ -537,18 +548,7 @@ hamls_status hamls_replan(hamls_plan_t P, const double* nodes_xyz, const double*
   return build_nodes(P, nodes_xyz, node_weights, M, stream);
 }
 
-hamls_status hamls_fit(hamls_plan_t P, const double* values, double* coeffs, cudaStream_t s) {
-  if (!P || !values || !coeffs) return HAMLS_ERR_INVALID_ARG;
-  reset_status_kernel<<<1, 32, 0, s>>>(P->st, 0);
-  ++P->launches;
-  const double* dv = values;
-  if (!is_device_ptr(values)) {
-    HAMLS_TRY(cudaMemcpyAsync(P->in_vals, values, (size_t)P->M * sizeof(double), cudaMemcpyHostToDevice, s));
-    dv = P->in_vals;
-  }
-  stage_begin(P, 4, s);
-  stage_values(dv, P->perm, (int)P->M, P->sy, P->pf, !P->mixed, P->st, s, &P->launches);
-  stage_end(P, 4, s);
+static MlsArgs mls_args(hamls_plan_s* P) {
   MlsArgs a;
   memset(&a, 0, sizeof(a));
   a.nodes = node_cells(P);
@@ -587,11 +587,21 @@ hamls_status hamls_fit(hamls_plan_t P, const double* values, double* coeffs, cud
   a.guard_list = P->guard_list;
   a.st = P->st;
   a.num_sms = P->num_sms;
+  return a;
+}
+
+// steps 1-2 of a fit on staged values: gather with n(q), guard, solves
+static void run_step2(hamls_plan_s* P, cudaStream_t s) {
+  MlsArgs a = mls_args(P);
   stage_begin(P, 5, s);
   run_mls(a, P->mixed, s, &P->launches, 1);
   run_guard(support_args(P), s, &P->launches);
   run_mls(a, P->mixed, s, &P->launches, 2);
   stage_end(P, 5, s);
+}
+
+// step 3 from the grid values: ring FFT, Legendre quadrature, coefficients out
+static hamls_status run_step3(hamls_plan_s* P, double* coeffs, cudaStream_t s) {
   const bool dev_out = is_device_ptr(coeffs);
   QuadArgs q;
   memset(&q, 0, sizeof(q));
@@ -613,6 +623,85 @@ hamls_status hamls_fit(hamls_plan_t P, const double* values, double* coeffs, cud
   }
   P->last = s;
   return cuda_status(cudaGetLastError());
+}
+
+hamls_status hamls_fit(hamls_plan_t P, const double* values, double* coeffs, cudaStream_t s) {
+  if (!P || !values || !coeffs) return HAMLS_ERR_INVALID_ARG;
+  reset_status_kernel<<<1, 32, 0, s>>>(P->st, 0);
+  ++P->launches;
+  const double* dv = values;
+  if (!is_device_ptr(values)) {
+    HAMLS_TRY(cudaMemcpyAsync(P->in_vals, values, (size_t)P->M * sizeof(double), cudaMemcpyHostToDevice, s));
+    dv = P->in_vals;
+  }
+  stage_begin(P, 4, s);
+  stage_values(dv, P->perm, (int)P->M, P->sy, P->pf, !P->mixed, P->st, s, &P->launches);
+  stage_end(P, 4, s);
+  run_step2(P, s);
+  return run_step3(P, coeffs, s);
+}
+
+hamls_status hamls_refit_prepare(hamls_plan_t P, cudaStream_t s) {
+  if (!P) return HAMLS_ERR_INVALID_ARG;
+  P->op_valid = false;
+  // a fit with zero values: the Gram moments, n(q) and the guard for the nodes
+  reset_status_kernel<<<1, 32, 0, s>>>(P->st, 0);
+  ++P->launches;
+  HAMLS_TRY(cudaMemsetAsync(P->in_vals, 0, (size_t)P->M * sizeof(double), s));
+  stage_values(P->in_vals, P->perm, (int)P->M, P->sy, P->pf, !P->mixed, P->st, s, &P->launches);
+  run_step2(P, s);
+  // members per grid node (into the spare order-key buffer), their total
+  MlsArgs a = mls_args(P);
+  HAMLS_TRY(cudaMemsetAsync(&P->st->cnt[C_OP_TOTAL], 0, sizeof(unsigned long long), s));
+  run_refit_operator(a, P->mixed, 0, nullptr, P->okeys_alt, nullptr, nullptr, &P->st->cnt[C_OP_TOTAL], s,
+                     &P->launches);
+  unsigned long long total = 0;
+  HAMLS_TRY(cudaMemcpyAsync(&total, &P->st->cnt[C_OP_TOTAL], sizeof(total), cudaMemcpyDeviceToHost, s));
+  HAMLS_TRY(cudaStreamSynchronize(s));
+  if (total >= 0xFFFFFFFFull) return HAMLS_ERR_CAPACITY;
+  // one allocation: CSR start, columns, values, gamma
+  const size_t vsz = P->mixed ? sizeof(float) : sizeof(double);
+  auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t nrow = (size_t)P->MQ + 1, ny = (size_t)value_moment_count(P->K);
+  const size_t b_rows = up(nrow * 4), b_col = up(total * 4 + 4), b_val = up(total * vsz + vsz);
+  const size_t b_gamma = up((size_t)P->MQ * ny * sizeof(double));
+  const size_t need = b_rows + b_col + b_val + b_gamma + up((size_t)P->Mcap * sizeof(float));
+  if (P->op_bytes < need) {
+    if (P->op_mem) cudaFree(P->op_mem);
+    P->op_mem = nullptr;
+    P->op_bytes = 0;
+    HAMLS_TRY(cudaMalloc(&P->op_mem, need));
+    P->op_bytes = need;
+  }
+  char* base = reinterpret_cast<char*>(P->op_mem);
+  P->op_rows = reinterpret_cast<uint32_t*>(base);
+  P->op_col = reinterpret_cast<uint32_t*>(base + b_rows);
+  P->op_val = base + b_rows + b_col;
+  P->op_gamma = reinterpret_cast<double*>(base + b_rows + b_col + b_val);
+  P->op_yf = reinterpret_cast<float*>(base + b_rows + b_col + b_val + b_gamma);
+  HAMLS_TRY(cudaMemcpyAsync(P->op_rows, P->okeys_alt, (size_t)P->MQ * 4, cudaMemcpyDeviceToDevice, s));
+  HAMLS_TRY(cudaMemsetAsync(P->op_rows + P->MQ, 0, 4, s));
+  exclusive_scan_u32(P->op_rows, P->MQ + 1, P->counts, s, &P->launches);
+  run_refit_operator(a, P->mixed, 1, P->op_gamma, P->op_rows, P->op_col, P->op_val, nullptr, s, &P->launches);
+  P->op_nnz = total;
+  P->op_valid = true;
+  P->last = s;
+  return cuda_status(cudaGetLastError());
+}
+
+hamls_status hamls_refit(hamls_plan_t P, const double* values, double* coeffs, cudaStream_t s) {
+  if (!P || !values || !coeffs) return HAMLS_ERR_INVALID_ARG;
+  if (!P->op_valid) return HAMLS_ERR_INVALID_ARG;
+  const double* dv = values;
+  if (!is_device_ptr(values)) {
+    HAMLS_TRY(cudaMemcpyAsync(P->in_vals, values, (size_t)P->M * sizeof(double), cudaMemcpyHostToDevice, s));
+    dv = P->in_vals;
+  }
+  stage_begin(P, 5, s);
+  run_refit_apply(P->MQ, P->mixed, P->op_rows, P->op_col, P->op_val, dv, (int)P->M, P->op_yf, P->fgrid, P->st, s,
+                  &P->launches);
+  stage_end(P, 5, s);
+  return run_step3(P, coeffs, s);
 }
 
 hamls_status hamls_sync(hamls_plan_t P, int timeout_ms) {
@@ -671,6 +760,7 @@ hamls_status hamls_destroy(hamls_plan_t P) {
     }
   if (P->arena.base) cudaFree(P->arena.base);
   if (P->shep_mem) cudaFree(P->shep_mem);
+  if (P->op_mem) cudaFree(P->op_mem);
   if (P->st_host) cudaFreeHost(P->st_host);
   delete P;
   return HAMLS_OK;

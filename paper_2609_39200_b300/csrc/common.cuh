@@ -34,7 +34,7 @@ enum : unsigned {
 
 // device counters
 enum { C_SUM_N = 0, C_MIN_N, C_MAX_N, C_REG, C_GUARD, C_REDO, C_DROP, C_GUARD_LIST, C_REDO_LIST,
-       C_BATCH, C_TILE, C_KNN_CAND, C_KNN_SCAN, C_KNN_EXACT_FB, C_LIST_BATCH, C_NCOUNT };
+       C_BATCH, C_TILE, C_KNN_CAND, C_KNN_SCAN, C_KNN_EXACT_FB, C_LIST_BATCH, C_OP_TOTAL, C_NCOUNT };
 
 struct DevStatus {
   unsigned flags;
@@ -253,7 +253,7 @@ __device__ __forceinline__ void band_runs(const Cells& g, const Cap& c, int b, u
                                           uint32_t& n0, uint32_t& s1, uint32_t& n1) {
   n0 = n1 = 0;
   s0 = s1 = 0;
-  const int B = g.B, P = g.P;
+  const int P = g.P;
   // band b spans zeta in [-1 + 2b/B, -1 + 2(b+1)/B)
   const float4 eb = g.edge[b], et = g.edge[b + 1];
   const float ab = eb.x, bb = eb.y, z_bot = eb.z, at = et.x, bt = et.y, z_top = et.z;

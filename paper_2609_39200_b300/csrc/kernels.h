@@ -132,6 +132,16 @@ struct MlsArgs {
 // part 1: gather every grid node (moments, n(q), guard list);
 // part 2: gather the guard list again, then solve (and re-solve in FP64)
 void run_mls(const MlsArgs& a, bool mixed, cudaStream_t s, int64_t* launches, int part);
+// values-only refits: part 0 = row counts (rows[j], their sum added to
+// *total); part 1 = gamma per grid node, then the operator (rows = CSR start)
+void run_refit_operator(const MlsArgs& a, bool mixed, int part, double* gamma, uint32_t* rows, uint32_t* col,
+                        void* val, unsigned long long* total, cudaStream_t s, int64_t* launches);
+// f = A y over the plan's grid; val is float (MIXED, with y converted into
+// yf, M floats) or double (FP64)
+void run_refit_apply(int MQ, bool mixed, const uint32_t* rows, const uint32_t* col, const void* val,
+                     const double* y, int M, float* yf, double* f, DevStatus* st, cudaStream_t s,
+                     int64_t* launches);
+int value_moment_count(int K);
 int mls_moment_slots(int K);
 
 // ------------------------------------------------------------------- quad.cu

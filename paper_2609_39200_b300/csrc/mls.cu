@@ -211,6 +211,111 @@ __device__ __forceinline__ void accumulate(T (&acc)[Shape<K>::NV], T w, T u, T v
   }
 }
 
+// The value weights of the local problem. For fixed nodes the Gram moments,
+// chi and tau~ are fixed, and c1 is linear in the value moments my (Sec. 2.3:
+// beta and e = L^{-1} z carry the data, nothing else does):
+//   c1 = sum_k gamma_k my_k,
+//   gamma_0 = 1 / (W den),
+//   gamma_(a,b) = -h_j is_j isW / den for the basis direction j = (a, b),
+// with h = L^{-T} g, g_j = d_j / (1 + tau~ mu_deg(j)) (the adjoint of the
+// forward substitution, dropped directions contribute nothing). Same steps as
+// solve_local up to tau~; FP64 throughout.
+template <int K>
+__device__ void solve_gamma(const double* mw, const SolveParams& P, double* gamma) {
+  using S = double;
+  constexpr int m = Shape<K>::m, mm = m - 1, D2 = 2 * K, D1 = K;
+  const S W = mw[0];
+  S is[m];
+#pragma unroll
+  for (int j = 1; j < m; ++j) {
+    const S g = mw[midx(2 * ea_of(j), 2 * eb_of(j), D2)];
+    is[j] = g > S(0) ? rsqrt_t<S>(g) : S(0);
+  }
+  const S isW = rsqrt_t<S>(W);
+  S L[mm * (mm + 1) / 2];
+#pragma unroll
+  for (int i = 0; i < mm; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j)
+      L[tri(i, j)] = mw[midx(ea_of(i + 1) + ea_of(j + 1), eb_of(i + 1) + eb_of(j + 1), D2)] * is[i + 1] * is[j + 1];
+  S bv[mm];
+#pragma unroll
+  for (int j = 0; j < mm; ++j) bv[j] = mw[midx(ea_of(j + 1), eb_of(j + 1), D2)] * is[j + 1] * isW;
+  bool drop[mm];
+#pragma unroll
+  for (int j = 0; j < mm; ++j) {
+    S sjj = L[tri(j, j)];
+#pragma unroll
+    for (int k = 0; k < j; ++k) sjj -= L[tri(j, k)] * L[tri(j, k)];
+    drop[j] = !(sjj > S(P.floor_));
+    const S ljj = drop[j] ? S(0) : sqrt(sjj);
+    const S inv = drop[j] ? S(0) : S(1) / ljj;
+    L[tri(j, j)] = ljj;
+#pragma unroll
+    for (int i = j + 1; i < mm; ++i) {
+      S v = L[tri(i, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) v -= L[tri(i, k)] * L[tri(j, k)];
+      L[tri(i, j)] = v * inv;
+    }
+  }
+  S d[mm], inv[mm];
+  S Dl[K + 1];
+#pragma unroll
+  for (int l = 0; l <= K; ++l) Dl[l] = S(0);
+#pragma unroll
+  for (int j = 0; j < mm; ++j) {
+    S vb = bv[j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) vb -= L[tri(j, k)] * d[k];
+    inv[j] = drop[j] ? S(0) : S(1) / L[tri(j, j)];
+    d[j] = vb * inv[j];
+    Dl[deg_of(j + 1)] += d[j] * d[j];
+  }
+  S r0 = S(0);
+#pragma unroll
+  for (int l = 1; l <= K; ++l) r0 += Dl[l];
+  const S infv = S(1) / S(0);
+  const S chi = r0 < S(1) ? S(1) / (S(1) - r0) : infv;
+  S tt = S(0);
+  const S chiT = S(P.chiT);
+  if (chi > chiT) {
+    const S rstar = S(1) - S(1) / chiT;
+    S lo = S(0), hi = r0 / (S(P.mu[1]) * rstar);
+    for (int it = 0; it < 200; ++it) {
+      const S mid = S(0.5) * (lo + hi);
+      S r = S(0);
+#pragma unroll
+      for (int l = 1; l <= K; ++l) r += Dl[l] / (S(1) + mid * S(P.mu[l]));
+      if (r > rstar) lo = mid;
+      else hi = mid;
+      if (hi - lo <= S(1e-16) * hi) break;
+    }
+    const S tau = S(0.5) * (lo + hi);
+    S t = (chi == infv) ? S(1) : (chi - chiT) / (S(P.chiF) - chiT);
+    t = t < S(1) ? t : S(1);
+    tt = smoothstep3(t) * tau;
+  }
+  S f[K + 1], den = S(1);
+  f[0] = S(0);
+#pragma unroll
+  for (int l = 1; l <= K; ++l) {
+    f[l] = S(1) / (S(1) + tt * S(P.mu[l]));
+    den -= Dl[l] * f[l];
+  }
+  S h[mm];
+#pragma unroll
+  for (int j = mm - 1; j >= 0; --j) {
+    S v = f[deg_of(j + 1)] * d[j];
+#pragma unroll
+    for (int k = j + 1; k < mm; ++k) v -= L[tri(k, j)] * h[k];
+    h[j] = v * inv[j];
+  }
+  gamma[0] = S(1) / (W * den);
+#pragma unroll
+  for (int j = 0; j < mm; ++j) gamma[midx(ea_of(j + 1), eb_of(j + 1), D1)] = -h[j] * is[j + 1] * isW / den;
+}
+
 constexpr int MLS_WARPS = 4;
 
 // Warp reduce-scatter of up to 64 per-lane partial sums: five exchange steps
@@ -481,6 +586,217 @@ void run_mls(const MlsArgs& a, bool mixed, cudaStream_t s, int64_t* launches, in
     default: break;
   }
 }
+
+// ------------------------------------------------ values-only refits
+// The fit as a linear operator of the values for fixed nodes:
+//   f(q_j) = sum_{i in X(q_j)} A_ji y_i,  A_ji = w_i sum_k gamma_jk u_i^a_k v_i^b_k,
+// with gamma_j from solve_gamma on grid node j's Gram moments and (w_i, u_i,
+// v_i) the weight and tangent coordinates of the gather.
+
+// gamma per grid node (indexed by node, from the moments of its work position)
+template <int K, bool MIXED>
+__global__ void __launch_bounds__(128) gamma_kernel(MlsArgs a, SolveParams P, double* __restrict__ gamma) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  constexpr int NV = Shape<K>::NV, NM = Shape<K>::NM, NY = Shape<K>::NY, NVP = (NV + 1) & ~1;
+  const long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= a.MQ) return;
+  const T* src = reinterpret_cast<const T*>(a.mom) + pos * NVP;
+  double mw[NM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) mw[i] = (double)src[i];
+  double g[NY];
+  solve_gamma<K>(mw, P, g);
+  const int j = (int)a.order[pos];
+#pragma unroll
+  for (int i = 0; i < NY; ++i) gamma[(size_t)j * NY + i] = g[i];
+}
+
+// One warp per grid node: the members of its ball in the gather's order and
+// test, counted (FILL = false: rows[j], and the total) or written
+// (FILL = true: rows = CSR start; col = original node index, val = A_ji).
+template <int K, bool MIXED, bool FILL>
+__global__ void __launch_bounds__(128) op_rows_kernel(MlsArgs a, const double* __restrict__ gamma, uint32_t* rows,
+                                                      uint32_t* __restrict__ col, void* valv,
+                                                      unsigned long long* total) {
+  constexpr int NY = Shape<K>::NY, D1 = K;
+  const int lane = threadIdx.x & 31;
+  const int L = 2 * a.N + 2;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const unsigned below = (1u << lane) - 1u;
+  unsigned long long tot = 0;
+  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < a.MQ; j += nw) {
+    const int k = j / L, jj = j - k * L;
+    double gm[NY];
+#pragma unroll
+    for (int i = 0; i < NY; ++i) gm[i] = FILL ? gamma[(size_t)j * NY + i] : 0.0;
+    uint32_t pos = FILL ? rows[j] : 0u;
+    // A_ji from (w, u, v) in FP64
+    auto entry = [&](double w, double u, double v) {
+      double s = 0.0, vb = 1.0;
+#pragma unroll
+      for (int b = 0; b <= D1; ++b) {
+        double t = vb;
+#pragma unroll
+        for (int aa = 0; aa <= D1 - b; ++aa) {
+          s += gm[midx(aa, b, D1)] * t;
+          if (aa < D1 - b) t *= u;
+        }
+        if (b < D1) vb *= v;
+      }
+      return w * s;
+    };
+    if (MIXED) {
+      const float st = a.sf[k], ct = a.tf[k], cp = a.cpf[jj], sp = a.spf[jj];
+      const float qxf = st * cp, qyf = st * sp, qzf = ct;
+      const float df = a.deltaf[j], r2f = a.rho2f[j], idf = 1.f / df;
+      const float e1x = ct * cp * idf, e1y = ct * sp * idf, e1z = -st * idf;
+      const float e2x = -sp * idf, e2y = cp * idf;
+      const Cap cap = make_cap_f(qxf, qyf, qzf, df);
+      for_cap_candidates(a.nodes, cap, [&](bool valid, uint32_t idx) {
+        bool in = false;
+        float w = 0.f, u = 0.f, v = 0.f;
+        if (valid) {
+          const float4 p = a.nodes.pf[idx];
+          const float dx = p.x - qxf, dy = p.y - qyf, dz = p.z - qzf;
+          const float c2 = dx * dx + dy * dy + dz * dz;
+          in = c2 < r2f;
+          if (in && FILL) {
+            w = wendland(geodesic_from_chord2(c2) * idf);
+            if (a.swf) w *= a.swf[idx];
+            u = e1x * dx + e1y * dy + e1z * dz;
+            v = e2x * dx + e2y * dy;
+          }
+        }
+        const unsigned bal = __ballot_sync(FULL, in);
+        if (FILL && in) {
+          const uint32_t e = pos + __popc(bal & below);
+          col[e] = a.nodes.perm[idx];
+          reinterpret_cast<float*>(valv)[e] = (float)entry((double)w, (double)u, (double)v);
+        }
+        pos += __popc(bal);
+      });
+    } else {
+      const double st = a.ring_s[k], ct = a.ring_t[k], cp = a.cphi[jj], sp = a.sphi[jj];
+      const double qx = st * cp, qy = st * sp, qz = ct;
+      const double delta = a.delta[j], rho2 = a.rho2[j];
+      const double id = 1.0 / delta;
+      const double e1x = ct * cp * id, e1y = ct * sp * id, e1z = -st * id;
+      const double e2x = -sp * id, e2y = cp * id;
+      const float qxf = (float)qx, qyf = (float)qy, qzf = (float)qz;
+      const float hi_f = (float)(rho2 + 1e-6 * sqrt(rho2) + 1e-6 * rho2 + 1e-13);
+      const Cap cap = make_cap_f(qxf, qyf, qzf, a.deltaf[j]);
+      for_cap_candidates(a.nodes, cap, [&](bool valid, uint32_t idx) {
+        bool in = false;
+        double w = 0.0, u = 0.0, v = 0.0;
+        if (valid) {
+          const float4 p = a.nodes.pf[idx];
+          const float fx = p.x - qxf, fy = p.y - qyf, fz = p.z - qzf;
+          if (fx * fx + fy * fy + fz * fz <= hi_f) {
+            const double X = a.nodes.px[idx], Y = a.nodes.py[idx], Z = a.nodes.pz[idx];
+            const double c2 = chord2_exact(X, Y, Z, qx, qy, qz);
+            in = c2 < rho2;
+            if (in && FILL) {
+              const double dx = X - qx, dy = Y - qy, dz = Z - qz;
+              w = wendland(geodesic_from_chord2(c2) * id);
+              if (a.sw) w *= a.sw[idx];
+              u = e1x * dx + e1y * dy + e1z * dz;
+              v = e2x * dx + e2y * dy;
+            }
+          }
+        }
+        const unsigned bal = __ballot_sync(FULL, in);
+        if (FILL && in) {
+          const uint32_t e = pos + __popc(bal & below);
+          col[e] = a.nodes.perm[idx];
+          reinterpret_cast<double*>(valv)[e] = entry(w, u, v);
+        }
+        pos += __popc(bal);
+      });
+    }
+    if (!FILL && lane == 0) {
+      rows[j] = pos;
+      tot += pos;
+    }
+  }
+  if (!FILL && lane == 0 && tot) atomicAdd(total, tot);
+}
+
+// f(q_j) = sum A_ji y_i; one warp per grid node (rows run from ~30 to tens of
+// thousands of entries), lane partial sums reduced in a tree. V = double:
+// FP64 throughout; V = float: FP32 entries times FP32 values, the rounding
+// level of the MIXED form's FP32 moments.
+template <typename V>
+__global__ void __launch_bounds__(256) op_apply_kernel(int MQ, const uint32_t* __restrict__ rows,
+                                                       const uint32_t* __restrict__ col, const V* __restrict__ val,
+                                                       const V* __restrict__ y, double* __restrict__ f,
+                                                       DevStatus* st) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < MQ; j += nw) {
+    const uint32_t e0 = rows[j], e1 = rows[j + 1];
+    V s = V(0);
+    for (uint32_t e = e0 + lane; e < e1; e += 32) s += val[e] * y[col[e]];
+    s = warp_sum(s);
+    if (lane == 0) {
+      if (!isfinite(s)) set_flag(st, ST_NONFINITE);
+      f[j] = (double)s;
+    }
+  }
+}
+
+__global__ void to_float_kernel(const double* __restrict__ y, int n, float* __restrict__ yf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) yf[i] = (float)y[i];
+}
+
+template <int K, bool MIXED>
+static void launch_op(const MlsArgs& a, const SolveParams& P, int part, double* gamma, uint32_t* rows, uint32_t* col,
+                      void* val, unsigned long long* total, cudaStream_t s, int64_t* launches) {
+  const int wblocks = (a.MQ + 3) / 4 < 148 * 64 ? (a.MQ + 3) / 4 : 148 * 64;
+  if (part == 0) {
+    op_rows_kernel<K, MIXED, false><<<wblocks, 128, 0, s>>>(a, gamma, rows, col, val, total);
+    ++*launches;
+  } else {
+    gamma_kernel<K, MIXED><<<(a.MQ + 127) / 128, 128, 0, s>>>(a, P, gamma);
+    op_rows_kernel<K, MIXED, true><<<wblocks, 128, 0, s>>>(a, gamma, rows, col, val, total);
+    *launches += 2;
+  }
+}
+
+void run_refit_operator(const MlsArgs& a, bool mixed, int part, double* gamma, uint32_t* rows, uint32_t* col,
+                        void* val, unsigned long long* total, cudaStream_t s, int64_t* launches) {
+  SolveParams P;
+  P.chiT = a.chiT;
+  P.chiF = a.chiF;
+  P.floor_ = a.floor_;
+  for (int l = 0; l <= KMAX; ++l) P.mu[l] = a.mu[l];
+  switch (a.K * 2 + (mixed ? 1 : 0)) {
+    case 2: launch_op<1, false>(a, P, part, gamma, rows, col, val, total, s, launches); break;
+    case 3: launch_op<1, true>(a, P, part, gamma, rows, col, val, total, s, launches); break;
+    case 4: launch_op<2, false>(a, P, part, gamma, rows, col, val, total, s, launches); break;
+    case 5: launch_op<2, true>(a, P, part, gamma, rows, col, val, total, s, launches); break;
+    case 6: launch_op<3, false>(a, P, part, gamma, rows, col, val, total, s, launches); break;
+    case 7: launch_op<3, true>(a, P, part, gamma, rows, col, val, total, s, launches); break;
+    case 8: launch_op<4, false>(a, P, part, gamma, rows, col, val, total, s, launches); break;
+    case 9: launch_op<4, true>(a, P, part, gamma, rows, col, val, total, s, launches); break;
+    default: break;
+  }
+}
+
+void run_refit_apply(int MQ, bool mixed, const uint32_t* rows, const uint32_t* col, const void* val,
+                     const double* y, int M, float* yf, double* f, DevStatus* st, cudaStream_t s, int64_t* launches) {
+  const int blocks = (MQ + 7) / 8 < 148 * 64 ? (MQ + 7) / 8 : 148 * 64;
+  if (mixed) {
+    to_float_kernel<<<(M + 255) / 256, 256, 0, s>>>(y, M, yf);
+    op_apply_kernel<float><<<blocks, 256, 0, s>>>(MQ, rows, col, reinterpret_cast<const float*>(val), yf, f, st);
+    *launches += 2;
+  } else {
+    op_apply_kernel<double><<<blocks, 256, 0, s>>>(MQ, rows, col, reinterpret_cast<const double*>(val), y, f, st);
+    ++*launches;
+  }
+}
+
+int value_moment_count(int K) { return (K + 1) * (K + 2) / 2; }
 
 int mls_moment_slots(int K) {
   const int nv = dim_tan(2 * K) + dim_tan(K);
