@@ -148,10 +148,6 @@ __device__ __forceinline__ float cell_coord_f(float x, float y, int P) {
   return ((float)q + frac) * (float)(P / 4);
 }
 
-__device__ __forceinline__ float zeta_to_z(float zeta) {
-  return zeta >= 0.f ? 1.f - (1.f - zeta) * (1.f - zeta) : (1.f + zeta) * (1.f + zeta) - 1.f;
-}
-
 // ------------------------------------------------------------- cap queries
 // Geodesic cap of radius r around a unit vector q, prepared for candidate
 // enumeration in FP32. Every margin enlarges the enumerated set; the caller
@@ -310,28 +306,7 @@ __device__ __forceinline__ void cap_band_range(const Cells& g, const Cap& c, int
 // instructions side by side on their own queries. Loops run while any group
 // still has work (warp-wide votes keep the warp converged); a group without
 // work takes part with neutral values.
-template <int G, typename T>
-__device__ __forceinline__ T group_sum(T v) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o, G);
-  return v;
-}
-
-template <int G>
-__device__ __forceinline__ float group_max(float v) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o, G));
-  return v;
-}
-
-// the group's lanes of a warp ballot, bit 0 = the group's first lane
-template <int G>
-__device__ __forceinline__ unsigned group_ballot(bool p) {
-  const unsigned b = __ballot_sync(FULL, p);
-  if (G == 32) return b;
-  return (b >> ((threadIdx.x & 31) & ~(G - 1))) & ((1u << (G & 31)) - 1u);
-}
-
+//
 // Group-cooperative enumeration of every sorted point index that can lie in
 // the cap. The runs of G consecutive bands are concatenated and dealt to the
 // group's lanes G at a time, so consecutive lanes read consecutive points.
