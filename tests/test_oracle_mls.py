@@ -318,3 +318,25 @@ def test_cell_keys_invariants():
     assert start[0] == 0 and start[-1] == len(x)
     cnt = np.bincount(k, minlength=bands * cells)
     assert np.array_equal(np.diff(start), cnt)
+
+
+def test_grid_values_linear_in_the_data_at_fixed_nodes():
+    # Sec. 2.3: the local Gram matrix, chi and tau~ depend on the nodes only
+    # and the data enter the regularised local problem through its right-hand
+    # side, so for fixed nodes every grid value is linear in y - also where
+    # the regularisation is active (the premise of values-only refits).
+    x = O.fibonacci_points(1500)
+    keep = x @ np.array([0.0, 0.6, 0.8]) < np.cos(0.5)        # a hole forces regularised nodes
+    x = x[keep]
+    rng = np.random.default_rng(5)
+    y1 = rng.standard_normal(len(x))
+    y2 = np.sin(3 * x[:, 0]) + x[:, 1] * x[:, 2]
+    N, K = 6, 2
+    r1 = O.hamls(x, y1, N, K, O.Params())
+    r2 = O.hamls(x, y2, N, K, O.Params())
+    r3 = O.hamls(x, y1 - 2.5 * y2, N, K, O.Params())
+    assert (r1.tau_tilde > 0).any()
+    np.testing.assert_array_equal(r1.tau_tilde, r2.tau_tilde)
+    lin = r1.fgrid - LD(2.5) * r2.fgrid
+    assert np.max(np.abs(r3.fgrid - lin)) < 1e-14 * np.max(np.abs(r3.fgrid))
+    assert np.linalg.norm(r3.coeffs - (r1.coeffs - 2.5 * r2.coeffs)) < 1e-13 * np.linalg.norm(r3.coeffs)
