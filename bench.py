@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=48, help="grid nodes the oracle evaluates for the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-csv", default=None, help="also write the clock samples here ({rank} = the rank)")
     ap.add_argument("--quick", action="store_true", help="skip the FP64 form, e2e and CPU baseline (profiling)")
     ap.add_argument("--cache", default=None, help="directory to keep/reuse the generated workload (profiling runs)")
     ap.add_argument("--fp64-pivot", type=float, default=None, help="mixed form: squared FP32 pivot below which a "
@@ -140,7 +141,7 @@ def aggregate_fits_per_s(steps_per_rank: int, local_seconds: float, world: int, 
 class Clocks:
     """SM clock and throttle reasons sampled during the timed region: NVML
     polled every 10 ms from a thread (nvidia-smi at 50 ms if NVML is
-    unavailable). Samples go to gpurun_out/clocks_rank<i>.csv as well."""
+    unavailable); with a path, the samples are also written there as CSV."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -148,13 +149,13 @@ class Clocks:
     REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
                ("sw_power_cap", 0x4))
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, path=None):
         self.index = index
         self.p = None
         self.thread = None
         self.rows = []
         self.nvml_error = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = path.replace("{rank}", str(index)) if path else None
 
     def _poll(self, nv, h):
         while not self.stop.is_set():
@@ -170,7 +171,8 @@ class Clocks:
 
     def __enter__(self):
         import threading
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        if self.path and os.path.dirname(self.path):
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
         try:
             import pynvml as nv
             nv.nvmlInit()
@@ -182,8 +184,10 @@ class Clocks:
         except Exception as e:
             self.thread = None
             self.nvml_error = f"{type(e).__name__}: {e}"[:120]
+        import tempfile
+        self.smi_path = self.path or os.path.join(tempfile.gettempdir(), f"hamls_clocks_{os.getpid()}_{self.index}.csv")
         try:
-            self.fh = open(self.path, "w")
+            self.fh = open(self.smi_path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv",
                                        "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
@@ -194,10 +198,11 @@ class Clocks:
         if self.thread is not None:
             self.stop.set()
             self.thread.join(timeout=5)
-            with open(self.path, "w") as fh:
-                fh.write("sm_mhz,max_sm_mhz,event_reasons,power_w\n")
-                for r in self.rows:
-                    fh.write(f"{r[0]},{r[1]},{r[2]:#x},{r[3]:.1f}\n")
+            if self.path:
+                with open(self.path, "w") as fh:
+                    fh.write("sm_mhz,max_sm_mhz,event_reasons,power_w\n")
+                    for r in self.rows:
+                        fh.write(f"{r[0]},{r[1]},{r[2]:#x},{r[3]:.1f}\n")
         if self.p is not None:
             self.p.terminate()
             try:
@@ -213,9 +218,9 @@ class Clocks:
             reasons = sorted({n for r in self.rows for n, bit in self.REASONS if r[2] & bit})
             return {"sm_mhz": float(np.median([r[0] for r in self.rows])), "sm_max_mhz": max(r[1] for r in self.rows),
                     "reasons": reasons, "samples": len(self.rows), "source": "nvml, 10 ms"}
-        if self.p is None or not os.path.exists(self.path):
+        if self.p is None or not os.path.exists(self.smi_path):
             return None
-        rows = [l.strip().split(", ") for l in open(self.path) if l.strip() and not l.startswith("index")]
+        rows = [l.strip().split(", ") for l in open(self.smi_path) if l.strip() and not l.startswith("index")]
         if not rows:
             return None
         mhz = [float(r[1].split()[0]) for r in rows if len(r) > 2]
@@ -306,7 +311,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with Clocks(local) as clk:
+    with Clocks(local, args.clocks_csv) as clk:
         times, mls, stages, launches = timed_steps(plan, x, y, out, args.steps, args.warmup)
     torch.cuda.synchronize()
     if dist:

@@ -3,7 +3,8 @@ end, on seeded inputs (GPU only).
 
 Bars: bit-exact for cell keys, sort permutation, CSR runs, k-NN radii and
 local node sets; relative coefficient error <= 1e-10 for the FP64 form; the
-mixed form within the tolerance derived in the design doc (FP32 moments: <= 1e-4
+mixed form within a tolerance that follows from its FP32 moments (about
+1e-6 relative per moment, amplified by the conditioned local solves: <= 1e-4
 relative on the coefficients here) and within 1.05x of the oracle's error
 against the known truth."""
 import math
