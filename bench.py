@@ -39,6 +39,8 @@ TRAFFIC = {
     "aux_knn": 215_310_080,
     # profiles/mls_gather_kernel_s2_n512_k3_m4m.md (the MLS stage's main kernel): 80.6 + 50.4 MB
     "mls": 131_017_472,
+    # profiles/op_apply_kernel_s2_n512_k3_m4m.md (values-only refit): 561.2 + 7.4 MB
+    "refit": 568_606_976,
 }
 
 
@@ -355,7 +357,8 @@ def run_ours(args):
                  "ms_per_step": float(rts.mean()), "prepare_s": prep_s, "operator_entries": int(nnz),
                  "roofline": {"bound": "hbm", "kernel": "op_apply_kernel<float> (+ to_float_kernel)",
                               "achieved": op_bytes / (a_ms / 1000.0) / 1e9, "peak": None, "unit": "GB/s",
-                              "frac": None, "algorithmic_bytes_per_launch": int(op_bytes), "ms_per_launch": a_ms},
+                              "frac": None, "traffic": TRAFFIC.get("refit"),
+                              "algorithmic_bytes_per_launch": int(op_bytes), "ms_per_launch": a_ms},
                  "note": "new values at the plan's nodes: the stored operator, then ring FFT and Legendre"}
 
     # ---- e2e: host buffers through the C ABI, copies inside the timed region.
@@ -444,7 +447,14 @@ def run_ours(args):
     m_dim = (w.K + 1) * (w.K + 2) // 2
     n_nb = 4 * m_dim
     hc = (w.N + 2) // 2
+    B_cells = 16
+    while B_cells * B_cells * 4 < w.M and B_cells < 4096:
+        B_cells *= 2
     alg = {
+        # per node: xyz in (24 B), key and index out (8 B), three radix passes over (key, index) (16 B
+        # each), staging xyz in (24 B) and the FP64 + FP32 copies out (40 B); the CSR run table
+        "cells": ("keys_kernel + radix sort + csr_kernel + stage_points_kernel",
+                  w.M * (24 + 8 + 3 * 16 + 24 + 40) + 4 * (B_cells * 2 * B_cells + 1)),
         # n nearest FP32 node records (x, y, z, y) per auxiliary point + its FP64 coordinates + d_n out
         "aux_knn": ("aux_knn_kernel", stats["aux_points"] * (16 * n_nb + 24 + 8)),
         # gathered FP32 node records + per grid node delta, rho2 (in), f (out), order key
@@ -466,7 +476,7 @@ def run_ours(args):
     if refit is not None:
         refit["roofline"]["peak"] = hbm_peak
         refit["roofline"]["frac"] = refit["roofline"]["achieved"] / hbm_peak
-    dom = max(stages, key=lambda k: stages[k])
+    dom = max(alg, key=lambda k: stages.get(k, 0.0))      # the slowest stage with a byte count
     dr = stage_roof.get(dom)
     roof = {"bound": "hbm", "kernel": dr["kernel"] if dr else dom, "achieved": dr["achieved_gbs"] if dr else None,
             "peak": hbm_peak, "unit": "GB/s", "frac": dr["frac"] if dr else None,
