@@ -1,8 +1,11 @@
 // api.cu - the C ABI of the HAMLS library (include/hamls.h, include/hamls_debug.h).
 //
 // A plan owns one device arena sized at creation for its capacity M, its
-// bandwidth N and degree K; hamls_replan and hamls_fit never allocate. Every
-// stage runs on the caller's stream; the host is never consulted in between.
+// bandwidth N and degree K, plus the Shepard operator (sized at plan time
+// after its members are counted: the one host wait of hamls_plan) and, once
+// hamls_refit_prepare has run, the refit operator (sized the same way).
+// hamls_replan, hamls_fit and hamls_refit never allocate. Every stage runs on
+// the caller's stream; those three calls never wait for the device.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdlib.h>

@@ -1,11 +1,16 @@
 // knn.cu - the adaptive support radius of Sec. 2.2.
 //
 //   d_n(a)   distance to the n-th nearest node (eq. adaptive_support_radius),
-//            at every point of a Fibonacci auxiliary grid;
+//            at every point of a Fibonacci auxiliary grid (aux_knn_kernel);
 //   d~_n(q)  its degree-zero MLS (Shepard) approximation with a constant
-//            support radius rho_aux, at every quadrature node q;
-//   delta(q) = (1 + eps) d~_n(q);  n(q) = #X(q) (eq. number_of_local_nodes);
-//   guard    if n(q) < m, delta(q) = (1 + eps) d_n(q) computed exactly at q.
+//            support radius rho_aux, at every quadrature node q: the members
+//            and weights depend on the plan only and are stored once as a
+//            sparse operator (shepard_rows_kernel), applied per replan
+//            (shepard_apply_kernel);
+//   delta(q) = (1 + eps) d~_n(q); n(q) = #X(q) (eq. number_of_local_nodes) is
+//            counted by the MLS gather;
+//   guard    if n(q) < m, delta(q) = (1 + eps) d_n(q) computed exactly at q
+//            (guard_kernel, inside the fit, for the positions the gather lists).
 //
 // All searches are warp-per-query over the band/cell structure. Membership is
 // decided on exact FP64 squared chords ((dx*dx + dy*dy) + dz*dz, no FMA); FP32

@@ -22,8 +22,12 @@
 //
 // Execution: the gather kernel gives each grid node (heaviest first) to one
 // warp: the 32 lanes stream its candidates (coalesced runs of the sorted
-// points), test the ball, accumulate the moments and reduce-scatter them into
-// a moment buffer. The solve kernel then runs one local problem per thread.
+// points), test the ball, count n(q), accumulate the moments and
+// reduce-scatter them into a moment buffer. The solve kernel then runs one
+// local problem per thread.
+//
+// Values-only refits (end of this file): for fixed nodes c_1 is linear in the
+// value moments, so the fit is stored as a sparse operator of the values.
 //
 // Precision forms: FP64 (everything in double) and MIXED (FP32 gather and
 // moments on centred, delta-scaled coordinates, FP32 solve; nodes whose FP32
