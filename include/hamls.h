@@ -25,7 +25,8 @@
  * host pointer (pageable or pinned); the library detects which with
  * cudaPointerGetAttributes and stages host data through buffers the plan owns.
  * The caller owns all argument buffers; the plan owns every device allocation
- * it makes (all of them inside hamls_plan, none in hamls_replan/hamls_fit).
+ * it makes: inside hamls_plan, and the refit operator in hamls_refit_prepare;
+ * hamls_replan, hamls_fit and hamls_refit allocate nothing.
  * Calls are stream-ordered and asynchronous: inputs must stay valid, and
  * outputs must not be read, until the stream work is done (hamls_sync).
  * A plan must not be used from two streams at once.
