@@ -13,10 +13,8 @@
 //
 // Legendre quadrature. fhat_l^m = sum_k A^m[l, k] F_k(m) with the folded
 // matrix of grid.cu: for the northern columns c < hc the pair (c, N - c)
-// contributes A^m[l, c] (F_c + (-1)^{l+m} F_{N-c}). One block per order m
-// stages the even/odd folded vectors in shared memory; one warp per degree l
-// streams its matrix row (coalesced) and reduces with shuffles. A single fit
-// is a matrix-vector product bound by HBM bandwidth on the matrix.
+// contributes A^m[l, c] (F_c + (-1)^{l+m} F_{N-c}). A single fit is a
+// matrix-vector product bound by HBM bandwidth on the matrix.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -95,15 +93,22 @@ __global__ void __launch_bounds__(256) ring_fft_kernel(const double* __restrict_
   }
 }
 
+// One block per (order m, 32 consecutive degrees l): the even/odd folded
+// vectors of order m go to shared memory, and each warp streams four matrix
+// rows at once (coalesced, four loads in flight), reducing with shuffles.
+constexpr int LEG_ROWS = 32;
+
 template <typename T>
 __global__ void __launch_bounds__(256) legendre_kernel(int N, int hc, const T* __restrict__ A,
                                                        const typename C2<T>::t* __restrict__ F,
                                                        double* __restrict__ coeffs) {
   using cT = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = blockIdx.x;
+  const int l0 = m + blockIdx.y * LEG_ROWS;
+  if (l0 > N) return;
   cT* E = reinterpret_cast<cT*>(smem_raw);
   cT* O = E + hc;
-  const int m = blockIdx.x;
   for (int c = threadIdx.x; c < hc; c += blockDim.x) {
     const cT a = F[(size_t)c * (N + 1) + m];
     const int cs = N - c;
@@ -119,22 +124,37 @@ __global__ void __launch_bounds__(256) legendre_kernel(int N, int hc, const T* _
     }
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t row0 = (size_t)m * (N + 1) - (size_t)m * (m - 1) / 2;
-  for (int l = m + warp; l <= N; l += nw) {
-    const cT* G = ((l + m) & 1) ? O : E;
-    const T* row = A + (row0 + (l - m)) * hc;
-    T sr = 0, si = 0;
-    for (int c = lane; c < hc; c += 32) {
-      const T av = row[c];
-      sr += av * G[c].x;
-      si += av * G[c].y;
+  const int lw = l0 + warp * 4;                     // this warp's first degree
+  T sr[4], si[4];
+  const T* row[4];
+  bool on[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    sr[r] = si[r] = T(0);
+    on[r] = lw + r <= N;
+    row[r] = A + (row0 + (on[r] ? lw + r - m : 0)) * hc;
+  }
+  for (int c = lane; c < hc; c += 32) {
+    T av[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) av[r] = on[r] ? row[r][c] : T(0);
+    const cT e = E[c], o = O[c];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const cT g = ((lw + r + m) & 1) ? o : e;
+      sr[r] += av[r] * g.x;
+      si[r] += av[r] * g.y;
     }
-    sr = warp_sum(sr);
-    si = warp_sum(si);
-    if (lane == 0) {
-      coeffs[2 * (row0 + (l - m))] = (double)sr;
-      coeffs[2 * (row0 + (l - m)) + 1] = (double)si;
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const T xr = warp_sum(sr[r]), xi = warp_sum(si[r]);
+    if (lane == 0 && on[r]) {
+      const size_t o = row0 + (size_t)(lw + r - m);
+      coeffs[2 * o] = (double)xr;
+      coeffs[2 * o + 1] = (double)xi;
     }
   }
 }
@@ -157,7 +177,8 @@ static void launch_quad(const QuadArgs& a, const typename C2<T>::t* W, const T* 
     ++*launches;
   }
   if (part & 2) {
-    legendre_kernel<T><<<N + 1, 256, smem_leg, s>>>(N, hc, A, reinterpret_cast<const cT*>(a.F), a.coeffs);
+    const dim3 grid(N + 1, (N + 1 + LEG_ROWS - 1) / LEG_ROWS);
+    legendre_kernel<T><<<grid, 256, smem_leg, s>>>(N, hc, A, reinterpret_cast<const cT*>(a.F), a.coeffs);
     ++*launches;
   }
 }
