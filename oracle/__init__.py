@@ -6,3 +6,4 @@ benchmark's CPU-baseline leg may import it. The product path never calls it
 and shares no code with it.
 """
 from .hamls_oracle import *  # noqa: F401,F403
+from .voronoi import voronoi_areas, voronoi_area_at  # noqa: F401
