@@ -58,7 +58,9 @@ typedef enum {
   HAMLS_ERR_SUPPORT_TOO_LARGE = 5,  /* delta(q) >= pi/2: no open hemisphere (Sec. 2.3) */
   HAMLS_ERR_TIMEOUT = 6,            /* hamls_sync gave up waiting */
   HAMLS_ERR_NONFINITE = 7,          /* a value or node coordinate is NaN/Inf */
-  HAMLS_ERR_CAPACITY = 8            /* M exceeds the plan's capacity */
+  HAMLS_ERR_CAPACITY = 8,           /* M exceeds the plan's capacity */
+  HAMLS_ERR_VORONOI = 9             /* a Voronoi cell reaches 1.5 rad from its node or needs more
+                                       than 32 edges (hamls_voronoi_areas/_weights) */
 } hamls_status;
 
 typedef enum { HAMLS_FP64 = 0, HAMLS_MIXED = 1 } hamls_precision;
@@ -169,6 +171,31 @@ hamls_status hamls_fit(hamls_plan_t plan, const double* values, double* coeffs, 
  */
 hamls_status hamls_refit_prepare(hamls_plan_t plan, cudaStream_t stream);
 hamls_status hamls_refit(hamls_plan_t plan, const double* values, double* coeffs, cudaStream_t stream);
+
+/*
+ * hamls_voronoi_areas - the area of the spherical Voronoi cell of every node
+ * of the plan, V_i = { p in S^2 : p.x_i >= p.x_j for all j }: the weights v_i
+ * by which the paper rescales the local MLS weights for ill-distributed nodes
+ * (Sec. 2.2, the remark after Theorem 2.1; all experiments of Sec. 3 use them).
+ *   areas   M doubles (host or device), in the node order of the last
+ *           hamls_plan/hamls_replan; they sum to 4 pi
+ * Exact duplicate nodes share their cell equally. Geometry in FP64 for FP64
+ * plans, FP32 (on FP64 differences of the nodes) for mixed plans. A cell that
+ * reaches 1.5 rad from its node (nodes confined to a small part of the
+ * sphere) or needs more than 32 edges gets a NaN area, and hamls_sync returns
+ * HAMLS_ERR_VORONOI. Allocates nothing; asynchronous on `stream`.
+ * Returns HAMLS_OK, HAMLS_ERR_INVALID_ARG or HAMLS_ERR_CUDA.
+ */
+hamls_status hamls_voronoi_areas(hamls_plan_t plan, double* areas, cudaStream_t stream);
+
+/*
+ * hamls_voronoi_weights - compute the Voronoi areas of the plan's nodes (as in
+ * hamls_voronoi_areas) and use them as the node weights v_i of the following
+ * fits, in place of the weights given to hamls_plan/hamls_replan, until the
+ * next hamls_replan. A refit operator prepared before is invalidated.
+ * Allocates nothing; asynchronous on `stream`.
+ */
+hamls_status hamls_voronoi_weights(hamls_plan_t plan, cudaStream_t stream);
 
 /* Wait (at most timeout_ms, < 0 = forever) for the plan's stream work and
  * return the first device-detected error, or HAMLS_OK. Clears the status. */

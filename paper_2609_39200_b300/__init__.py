@@ -25,8 +25,9 @@ LIB_PATH = os.path.join(_HERE, "libhamls.so")
 
 HAMLS_FP64, HAMLS_MIXED = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "cuda error", 4: "underdetermined",
-          5: "support too large", 6: "timeout", 7: "non-finite value", 8: "capacity exceeded"}
-STAGES = ("cells", "aux_knn", "shepard", "order", "stage_values", "mls", "fft", "legendre")
+          5: "support too large", 6: "timeout", 7: "non-finite value", 8: "capacity exceeded",
+          9: "voronoi cell failed"}
+STAGES = ("cells", "aux_knn", "shepard", "order", "stage_values", "mls", "fft", "legendre", "voronoi")
 
 
 class HamlsError(RuntimeError):
@@ -62,6 +63,8 @@ _SIGS = {
     "hamls_fit": (_I, [_P, _P, _P, _P]),
     "hamls_refit_prepare": (_I, [_P, _P]),
     "hamls_refit": (_I, [_P, _P, _P, _P]),
+    "hamls_voronoi_areas": (_I, [_P, _P, _P]),
+    "hamls_voronoi_weights": (_I, [_P, _P]),
     "hamls_sync": (_I, [_P, _I]),
     "hamls_stats": (_I, [_P, ctypes.POINTER(FitStats)]),
     "hamls_destroy": (_I, [_P]),
@@ -181,6 +184,19 @@ class Plan:
         self._keep_refit = (values, out)
         _check(lib().hamls_refit(self.h, _ptr(values), _ptr(out), _stream(stream)), "hamls_refit")
         return out
+
+    def voronoi_areas(self, out=None, stream=None):
+        """Areas of the spherical Voronoi cells of the plan's nodes (M float64,
+        node order). ``out`` may be a device tensor or a host tensor."""
+        if out is None:
+            out = torch.empty(self.M, dtype=torch.float64, device="cuda")
+        self._keep_vor = out
+        _check(lib().hamls_voronoi_areas(self.h, _ptr(out), _stream(stream)), "hamls_voronoi_areas")
+        return out
+
+    def voronoi_weights(self, stream=None):
+        """Use the Voronoi areas of the current nodes as the weights v_i."""
+        _check(lib().hamls_voronoi_weights(self.h, _stream(stream)), "hamls_voronoi_weights")
 
     def sync(self, timeout_ms: int = -1):
         _check(lib().hamls_sync(self.h, int(timeout_ms)), "hamls_sync")

@@ -25,7 +25,7 @@ static int dim_tan_host(int K) { return (K + 1) * (K + 2) / 2; }
 
 namespace {
 
-constexpr int NSTAGE = 8;
+constexpr int NSTAGE = 9;
 
 struct Arena {
   char* base = nullptr;
@@ -476,6 +476,7 @@ const char* hamls_status_string(hamls_status s) {
     case HAMLS_ERR_TIMEOUT: return "timed out waiting for the device";
     case HAMLS_ERR_NONFINITE: return "non-finite value";
     case HAMLS_ERR_CAPACITY: return "node count exceeds the plan capacity";
+    case HAMLS_ERR_VORONOI: return "a Voronoi cell reaches 1.5 rad from its node or needs more than 32 edges";
   }
   return "unknown status";
 }
@@ -707,6 +708,35 @@ hamls_status hamls_refit(hamls_plan_t P, const double* values, double* coeffs, c
   return run_step3(P, coeffs, s);
 }
 
+// Voronoi areas of the plan's nodes (Sec. 2.2, after Theorem 2.1): into the
+// caller's buffer, or into the plan's node weights v_i. The FP32 remainders of
+// the nodes go to the host-node staging buffer (M x 3 doubles), which a
+// replan only needs before its cell build.
+static float4* vor_scratch(hamls_plan_s* P) { return reinterpret_cast<float4*>(P->in_nodes); }
+
+hamls_status hamls_voronoi_areas(hamls_plan_t P, double* areas, cudaStream_t s) {
+  if (!P || !areas) return HAMLS_ERR_INVALID_ARG;
+  const bool dev = is_device_ptr(areas);
+  double* dst = dev ? areas : P->in_vals;
+  stage_begin(P, 8, s);
+  run_voronoi(node_cells(P), P->mixed, vor_scratch(P), dst, nullptr, nullptr, P->st, s, &P->launches);
+  stage_end(P, 8, s);
+  if (!dev) HAMLS_TRY(cudaMemcpyAsync(areas, dst, (size_t)P->M * sizeof(double), cudaMemcpyDeviceToHost, s));
+  P->last = s;
+  return cuda_status(cudaGetLastError());
+}
+
+hamls_status hamls_voronoi_weights(hamls_plan_t P, cudaStream_t s) {
+  if (!P) return HAMLS_ERR_INVALID_ARG;
+  stage_begin(P, 8, s);
+  run_voronoi(node_cells(P), P->mixed, vor_scratch(P), nullptr, P->sw, P->swf, P->st, s, &P->launches);
+  stage_end(P, 8, s);
+  P->has_weights = true;
+  P->op_valid = false;   // the refit operator holds the old weights
+  P->last = s;
+  return cuda_status(cudaGetLastError());
+}
+
 hamls_status hamls_sync(hamls_plan_t P, int timeout_ms) {
   if (!P) return HAMLS_ERR_INVALID_ARG;
   cudaStream_t s = P->last;
@@ -728,6 +758,7 @@ hamls_status hamls_sync(hamls_plan_t P, int timeout_ms) {
   if (f & ST_NONFINITE) return HAMLS_ERR_NONFINITE;
   if (f & ST_SUPPORT) return HAMLS_ERR_SUPPORT_TOO_LARGE;
   if (f & (ST_UNDERDET | ST_KNN)) return HAMLS_ERR_UNDERDETERMINED;
+  if (f & ST_VORONOI) return HAMLS_ERR_VORONOI;
   return HAMLS_OK;
 }
 

@@ -30,6 +30,7 @@ enum : unsigned {
   ST_NONFINITE = 4u,    // non-finite value
   ST_BADNODE = 8u,      // node not a unit vector / not finite
   ST_KNN = 16u,         // k-nearest-neighbour search did not converge (M < n)
+  ST_VORONOI = 32u,     // a Voronoi cell could not be formed (reaches 1.5 rad, > 32 edges)
 };
 
 // device counters

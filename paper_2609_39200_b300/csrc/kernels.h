@@ -156,4 +156,11 @@ struct QuadArgs {
 // part: 1 = ring FFT, 2 = Legendre contraction, 3 = both
 void run_quadrature(const QuadArgs& a, bool mixed, cudaStream_t s, int64_t* launches, int part = 3);
 
+// ---------------------------------------------------------------- voronoi.cu
+// Area of the spherical Voronoi cell of every point of g (FP32 area when
+// mixed, FP64 otherwise): written to out[perm[s]], sw[s] and swf[s] for the
+// non-null ones; lo_scratch holds g.n float4 (overwritten).
+void run_voronoi(const Cells& g, bool mixed, float4* lo_scratch, double* out, double* sw, float* swf,
+                 DevStatus* st, cudaStream_t s, int64_t* launches);
+
 }  // namespace hamls
