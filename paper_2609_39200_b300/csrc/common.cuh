@@ -317,15 +317,21 @@ __device__ __forceinline__ void cap_band_range(const Cells& g, const Cap& c, int
 // With MIDOUT the bands are visited from the cap centre's band outwards
 // (offsets 0, +1, -1, +2, -2, ...), so candidates arrive roughly nearest
 // first; searches that keep the n nearest then rarely update after a while.
-template <int G, bool MIDOUT = false, class F>
-__device__ __forceinline__ void for_cap_candidates_g(const Cells& g, const Cap& c, bool active, F&& f) {
+// stop() (warp-uniform) ends the enumeration early; the default never does.
+struct NoStop {
+  __device__ __forceinline__ constexpr bool operator()() const { return false; }
+};
+
+template <int G, bool MIDOUT = false, class F, class S = NoStop>
+__device__ __forceinline__ void for_cap_candidates_g(const Cells& g, const Cap& c, bool active, F&& f,
+                                                     S stop = S()) {
   const int gl = threadIdx.x & (G - 1);
   int b_lo, b_hi;
   cap_band_range(g, c, b_lo, b_hi);
   const int bc = MIDOUT ? min(max(band_of_f(c.zq, g.B), b_lo), b_hi) : b_lo;
   int span = MIDOUT ? 2 * max(bc - b_lo, b_hi - bc) + 1 : b_hi - b_lo + 1;
   if (!active) span = 0;
-  for (int k0 = 0; __any_sync(FULL, k0 < span); k0 += G) {
+  for (int k0 = 0; __any_sync(FULL, k0 < span) && !stop(); k0 += G) {
     const int k = k0 + gl;
     const int b = MIDOUT ? bc + ((k & 1) ? (k + 1) / 2 : -(k / 2)) : b_lo + k;
     uint32_t s0 = 0, n0 = 0, s1 = 0, n1 = 0;
@@ -339,7 +345,7 @@ __device__ __forceinline__ void for_cap_candidates_g(const Cells& g, const Cap& 
     }
     const uint32_t excl = incl - len;
     const uint32_t total = __shfl_sync(FULL, incl, G - 1, G);
-    for (uint32_t base = 0; __any_sync(FULL, base < total); base += G) {
+    for (uint32_t base = 0; __any_sync(FULL, base < total) && !stop(); base += G) {
       const uint32_t v = base + gl;
       int owner = 0;
 #pragma unroll
@@ -361,9 +367,9 @@ __device__ __forceinline__ void for_cap_candidates_g(const Cells& g, const Cap& 
 }
 
 // The warp-per-query enumeration (one group of 32 lanes).
-template <bool MIDOUT = false, class F>
-__device__ __forceinline__ void for_cap_candidates(const Cells& g, const Cap& c, F&& f) {
-  for_cap_candidates_g<32, MIDOUT>(g, c, true, f);
+template <bool MIDOUT = false, class F, class S = NoStop>
+__device__ __forceinline__ void for_cap_candidates(const Cells& g, const Cap& c, F&& f, S stop = S()) {
+  for_cap_candidates_g<32, MIDOUT>(g, c, true, f, stop);
 }
 
 // Number of candidates the enumeration would visit (no point is read).

@@ -22,11 +22,14 @@
 //     up to 4 r0, until every vertex is settled. A vertex c with
 //     |c - x_i| <= r / 2 (chords) is a vertex of V_i: a node of its flower
 //     cap lies within 2 |c - x_i| <= r of x_i;
-//  2. for every vertex still unsettled, the nodes of its own flower cap. For
-//     a cell at a hole's rim that cap is about the hole, whose cells hold no
-//     node.
-// A candidate whose line lies farther from the origin than every vertex
-// (h^2 >= R^2 (a^2 + b^2)) cannot cut and is skipped.
+//  2. for every vertex still unsettled, the nodes of its own flower cap: the
+//     first round that holds one cuts the vertex off by the node closest to
+//     it, and the search ends; the new vertices get searches of their own.
+//     A search that finds none settles the vertex. For a cell at a hole's
+//     rim the flower cap is about the hole, whose cells hold no node.
+// In step 1 a candidate whose line lies farther from the origin than every
+// vertex (h^2 >= R^2 (a^2 + b^2)) cannot cut; the others are tested against
+// every vertex at once, and only those that cut are clipped, one at a time.
 //
 // Precision. The clipping runs in FP32 on differences d taken from a hi/lo
 // split of the nodes (hi = the FP32 copy of the cell structure, lo = the FP32
@@ -169,9 +172,30 @@ __device__ __forceinline__ bool vor_clip(VPoly& P, float A, float B, float H, in
   return __all_sync(FULL, lane >= np || (isfinite(P.u) && isfinite(P.v)));
 }
 
-// One round of candidates (one per lane): clip by those that can cut, the
-// nearest first. Nodes with h below hskip were handled by a smaller cap.
-// Returns false on a polygon failure.
+// The half-plane of the node at sorted position idx (FP32, from the hi/lo
+// split). Returns false for an exact duplicate of the node.
+__device__ __forceinline__ bool vor_line(const Cells& g, const float4* __restrict__ lo, const VorNode& q,
+                                         uint32_t idx, float& a, float& b, float& h) {
+  const float4 ph = g.pf[idx], pl = lo[idx];
+  const float dx = (ph.x - q.hi.x) + (pl.x - q.lo.x);
+  const float dy = (ph.y - q.hi.y) + (pl.y - q.lo.y);
+  const float dz = (ph.z - q.hi.z) + (pl.z - q.lo.z);
+  a = q.e1.x * dx + q.e1.y * dy + q.e1.z * dz;
+  b = q.e2.x * dx + q.e2.y * dy + q.e2.z * dz;
+  h = 0.5f * (dx * dx + dy * dy + dz * dz);
+  return !(dx == 0.f && dy == 0.f && dz == 0.f);
+}
+
+// does the line u a + v b = h leave the point (u, v) outside (beyond rounding)
+__device__ __forceinline__ bool vor_outside(float a, float b, float h, float u, float v) {
+  return a * u + b * v - h > 8.f * VOR_EPS * (fabsf(a * u) + fabsf(b * v) + h);
+}
+
+// One round of candidates around the node (one per lane): skip those whose
+// line lies farther from the origin than every vertex, test the rest against
+// every vertex at once, and clip by the ones that cut, the nearest first.
+// Nodes with h below hskip were handled by a smaller cap. Returns false on a
+// polygon failure.
 __device__ __forceinline__ bool vor_round(const Cells& g, const float4* __restrict__ lo, const VorNode& q, VPoly& P,
                                           float& R2, bool valid, uint32_t idx, int& dups, bool count_dups,
                                           float hskip) {
@@ -179,24 +203,24 @@ __device__ __forceinline__ bool vor_round(const Cells& g, const float4* __restri
   float ca = 0.f, cb = 0.f, ch = 0.f;
   bool pend = valid && (int)idx != q.s;
   if (pend) {
-    const float4 ph = g.pf[idx], pl = lo[idx];
-    const float dx = (ph.x - q.hi.x) + (pl.x - q.lo.x);
-    const float dy = (ph.y - q.hi.y) + (pl.y - q.lo.y);
-    const float dz = (ph.z - q.hi.z) + (pl.z - q.lo.z);
-    if (dx == 0.f && dy == 0.f && dz == 0.f) {
+    if (!vor_line(g, lo, q, idx, ca, cb, ch)) {
       if (count_dups) ++dups;
       pend = false;
-    } else {
-      ca = q.e1.x * dx + q.e1.y * dy + q.e1.z * dz;
-      cb = q.e2.x * dx + q.e2.y * dy + q.e2.z * dz;
-      ch = 0.5f * (dx * dx + dy * dy + dz * dz);
-      if (!(ch > 0.f) || ch < hskip) pend = false;
+    } else if (!(ch > 0.f) || ch < hskip) {
+      pend = false;
     }
   }
   for (;;) {
     // the line lies h / |(a, b)| from the origin: it cuts only if that is
     // below the polygon's radius
     if (pend && !(ch * ch < R2 * 1.0001f * (ca * ca + cb * cb))) pend = false;
+    if (__ballot_sync(FULL, pend) == 0u) return true;
+    bool cut = false;
+    for (int k = 0; k < P.n; ++k) {
+      const float uk = __shfl_sync(FULL, P.u, k), vk = __shfl_sync(FULL, P.v, k);
+      cut = cut || vor_outside(ca, cb, ch, uk, vk);
+    }
+    pend = pend && cut;
     if (__ballot_sync(FULL, pend) == 0u) return true;
     const unsigned key = pend ? __float_as_uint(ch) : 0xffffffffu;
     const unsigned kmin = __reduce_min_sync(FULL, key);
@@ -207,6 +231,35 @@ __device__ __forceinline__ bool vor_round(const Cells& g, const float4* __restri
     if (__any_sync(FULL, lane < P.n && P.id == cid)) continue;   // already an edge
     if (!vor_clip(P, A, B, H, cid)) return false;
     R2 = vor_r2(P);
+  }
+}
+
+// One round of the flower cap of the vertex (fu, fv): the nodes closer to it
+// than x_i are exactly those whose line leaves it outside. Clip by the one
+// closest to the vertex (largest a fu + b fv - h, which is proportional to
+// p.x_j - p.x_i at the vertex p) and report the vertex as cut. Returns false
+// on a polygon failure.
+__device__ __forceinline__ bool vor_flower_round(const Cells& g, const float4* __restrict__ lo, const VorNode& q,
+                                                 VPoly& P, float& R2, bool valid, uint32_t idx, float fu, float fv,
+                                                 bool& cut_vertex) {
+  float ca = 0.f, cb = 0.f, ch = 0.f;
+  bool pend = valid && (int)idx != q.s;
+  if (pend) pend = vor_line(g, lo, q, idx, ca, cb, ch) && ch > 0.f && vor_outside(ca, cb, ch, fu, fv);
+  const int lane = threadIdx.x & 31;
+  const float depth = ca * fu + cb * fv - ch;
+  for (;;) {
+    if (__ballot_sync(FULL, pend) == 0u) return true;
+    const unsigned key = pend ? __float_as_uint(depth) : 0u;          // depth > 0 where pending
+    const unsigned kmax = __reduce_max_sync(FULL, key);
+    const int j = __ffs(__ballot_sync(FULL, pend && key == kmax)) - 1;
+    const float A = __shfl_sync(FULL, ca, j), B = __shfl_sync(FULL, cb, j), H = __shfl_sync(FULL, ch, j);
+    const int cid = __shfl_sync(FULL, (int)idx, j);
+    if (lane == j) pend = false;
+    if (__any_sync(FULL, lane < P.n && P.id == cid)) continue;   // already an edge
+    cut_vertex = true;
+    if (!vor_clip(P, A, B, H, cid)) return false;
+    R2 = vor_r2(P);
+    return true;
   }
 }
 
@@ -324,9 +377,14 @@ __global__ void __launch_bounds__(VOR_WARPS * 32) voronoi_kernel(Cells g, const 
         break;
       }
       const Cap cf = make_cap_f(cx * ic, cy * ic, cz * ic, rg);
-      for_cap_candidates<true>(g, cf, [&](bool valid, uint32_t idx) {
-        if (good) good = vor_round(g, lo, q, P, R2, valid, idx, dups, false, -1.f);
-      });
+      bool cut_vertex = false;
+      for_cap_candidates<true>(
+          g, cf,
+          [&](bool valid, uint32_t idx) {
+            if (good && !cut_vertex) good = vor_flower_round(g, lo, q, P, R2, valid, idx, fu, fv, cut_vertex);
+          },
+          [&]() { return cut_vertex || !good; });
+      // not cut: no node is closer to the vertex than x_i
       P.fin = P.fin || P.tag;
       P.tag = false;
     }
