@@ -300,7 +300,8 @@ def run_ours(args):
                 st = plan.stage_times()
                 mls.append(st["mls"])
                 for k, v in st.items():
-                    stage_sum[k] = stage_sum.get(k, 0.0) + v
+                    if v >= 0:                  # stages the step did not run report -1
+                        stage_sum[k] = stage_sum.get(k, 0.0) + v
         launches = plan.launch_count()
         plan.sync(600000)
         return np.array(times), np.array(mls), {k: v / steps for k, v in stage_sum.items()}, launches
@@ -361,6 +362,36 @@ def run_ours(args):
                               "algorithmic_bytes_per_launch": int(op_bytes), "ms_per_launch": a_ms},
                  "note": "new values at the plan's nodes: the stored operator, then ring FFT and Legendre"}
 
+    # ---- Voronoi areas of the nodes (the weights v_i of Sec. 2.2, computed once
+    # per node set): CUDA events around hamls_voronoi_areas, L2 flushed between calls
+    def voronoi_leg(pl, reps):
+        try:
+            pl.set_timing(False)
+            area = torch.empty(w.M, dtype=torch.float64, device=dev)
+            for _ in range(2):
+                pl.voronoi_areas(out=area)
+            pl.sync(600000)
+            ts = []
+            for i in range(reps):
+                flush.fill_(float(i))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pl.voronoi_areas(out=area)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            pl.sync(600000)
+            ms = float(np.mean(ts))
+            return {"ms": ms, "cells_per_s": w.M / (ms / 1000.0), "reps": reps,
+                    "area_sum_minus_4pi": float(area.sum()) - 4.0 * np.pi,
+                    "kernels": "vor_split_kernel + voronoi_kernel"}
+        except Exception as e:                  # reported, never fatal to the headline line
+            return {"error": f"{type(e).__name__}: {e}"}
+
+    voronoi = None
+    if not args.quick:
+        voronoi = {"mixed": voronoi_leg(plan, 10)}
+
     # ---- e2e: host buffers through the C ABI, copies inside the timed region.
     # Two plans on two streams take the steps in turn, as a caller with a
     # stream of fits would: one step's host-to-device copy overlaps the other
@@ -414,6 +445,8 @@ def run_ours(args):
         fp64 = {"value": world * len(t64) / (float(t64.sum()) / 1000.0), "unit": "fits/s",
                 "ms_per_step": float(t64.mean()), "mls_ms": float(m64.mean()),
                 "stage_ms": {k: round(v, 4) for k, v in st64.items()}}
+        if voronoi is not None:
+            voronoi["fp64"] = voronoi_leg(p64, 5)
         p64.close()
 
     # ---- accuracy against the known truth (eq. relative_error_S2, by Parseval)
@@ -495,7 +528,7 @@ def run_ours(args):
                 "grid_nodes_per_s": value * MQ,
                 "stage_ms": {k: round(v, 4) for k, v in stages.items()},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk.summary(), "fp64_form": fp64, "refit": refit, "l2_error": l2,
+                "clocks": clk.summary(), "fp64_form": fp64, "refit": refit, "voronoi": voronoi, "l2_error": l2,
                 "mls_stats": {k: stats[k] for k in ("sum_n", "min_n", "max_n", "n_regularized", "n_guarded",
                                                     "n_fp64_redo", "n_dropped")},
                 "knn_stats": {k: stats[k] for k in ("aux_points", "knn_candidates", "knn_scans",
