@@ -34,7 +34,7 @@
 // Precision. The clipping runs in FP32 on differences d taken from a hi/lo
 // split of the nodes (hi = the FP32 copy of the cell structure, lo = the FP32
 // rounding of the remainder), accurate to about 1e-7 relative, with no FP64
-// arithmetic per candidate (FP64 is slow on this part). Mixed plans take the
+// arithmetic per candidate (sm_103a runs FP64 at 1/64 of the FP32 rate). Mixed plans take the
 // area from the FP32 polygon. FP64 plans keep its edges (the nodes that bound
 // the cell) and recompute lines, vertices and area in FP64: a decision that
 // FP32 gets wrong near a degenerate vertex adds or drops an edge of relative
