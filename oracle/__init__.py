@@ -7,3 +7,4 @@ and shares no code with it.
 """
 from .hamls_oracle import *  # noqa: F401,F403
 from .voronoi import voronoi_areas, voronoi_area_at  # noqa: F401
+from .forward import complex_coeffs, forward, forward_full, global_lsq  # noqa: F401
