@@ -26,7 +26,7 @@
  * cudaPointerGetAttributes and stages host data through buffers the plan owns.
  * The caller owns all argument buffers; the plan owns every device allocation
  * it makes: inside hamls_plan, and the refit operator in hamls_refit_prepare;
- * hamls_replan, hamls_fit and hamls_refit allocate nothing.
+ * hamls_replan, hamls_fit, hamls_refit and the Voronoi calls allocate nothing.
  * Calls are stream-ordered and asynchronous: inputs must stay valid, and
  * outputs must not be read, until the stream work is done (hamls_sync).
  * A plan must not be used from two streams at once.
@@ -34,8 +34,8 @@
  * Errors. No exception crosses the ABI and the library never aborts the
  * process. Argument errors are returned immediately. Conditions found on the
  * device (too few nodes in a support, support radius >= pi/2, non-finite
- * values, nodes off the unit sphere) are recorded in a device status word and
- * returned by hamls_sync.
+ * values, nodes off the unit sphere, a Voronoi cell that cannot be formed)
+ * are recorded in a device status word and returned by hamls_sync.
  */
 #ifndef HAMLS_H
 #define HAMLS_H

@@ -44,6 +44,19 @@ def test_default_params_and_status_strings():
         assert h.lib().hamls_status_string(code)
 
 
+def test_status_codes_agree_between_header_binding_and_library():
+    # every hamls_status of the public header has a name in the binding and a
+    # distinct text in the library; the Voronoi calls report code 9
+    import paper_2609_39200_b300 as h
+    src = open(os.path.join(ROOT, "include", "hamls.h")).read()
+    enum = src[src.index("typedef enum {"):src.index("} hamls_status;")]
+    codes = {name: int(v) for name, v in re.findall(r"(HAMLS_(?:OK|ERR_[A-Z_]+))\s*=\s*(\d+)", enum)}
+    assert codes["HAMLS_ERR_VORONOI"] == 9
+    assert set(codes.values()) == set(h.STATUS)
+    texts = {h.lib().hamls_status_string(c) for c in codes.values()}
+    assert len(texts) == len(codes) and b"unknown status" not in texts
+
+
 def test_bad_arguments_rejected_on_host():
     import numpy as np
     import paper_2609_39200_b300 as h
