@@ -73,3 +73,18 @@ def test_bad_arguments_rejected_on_host():
     assert L.hamls_plan(None, x.ctypes.data, None, 100, 8, 2, ctypes.byref(p), None) == 1
     assert L.hamls_fit(None, None, None, None) == 1
     assert L.hamls_destroy(None) == 1
+
+
+def test_product_has_no_path_to_the_oracle_and_fails_loudly_without_the_library(monkeypatch):
+    # the package never imports the CPU oracle, and with its CUDA library
+    # missing it raises instead of computing anything another way
+    pkg = os.path.join(ROOT, "paper_2609_39200_b300")
+    for f in glob.glob(os.path.join(pkg, "*.py")):
+        src = open(f).read()
+        assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
+        assert "hamls_oracle" not in src, f
+    import paper_2609_39200_b300 as h
+    monkeypatch.setattr(h, "_lib", None)
+    monkeypatch.setattr(h, "LIB_PATH", os.path.join(pkg, "missing-libhamls.so"))
+    with pytest.raises(ImportError):
+        h.lib()
