@@ -17,4 +17,8 @@ from .gen import (  # noqa: F401
     synth_field,
     workload,
     WORKLOADS,
+    FitSpec,
+    batch_specs,
+    serving_trace,
+    fit_workload,
 )

@@ -306,3 +306,70 @@ def workload(name: str, fit_index: int = 0, M: Optional[int] = None, xp=np, devi
             f = synth_field(truth, tx, xp, chunk=1 << 22).cpu().numpy()
     noise = SplitMix64(seed).stream(13).normal(len(f)) * spec["noise"]
     return Workload(name, spec["N"], spec["K"], spec["M"], x, f + noise, truth, meta)
+
+
+# ---------------------------------------------------------------- many fits
+@dataclass
+class FitSpec:
+    """One fit of a batch or of a serving trace: sizes, holes and its seed."""
+    index: int
+    N: int
+    K: int
+    M: int
+    holes_deg: tuple
+    seed: int
+    arrival_s: float = 0.0      # serving traces: arrival time of the request
+
+
+BATCH_N = (32, 64, 128, 256)
+HOLES_DEG = (10.0, 20.0, 35.0)
+SERVE_N = (64, 128, 256, 512, 1024)
+SERVE_P = (0.30, 0.30, 0.20, 0.15, 0.05)
+
+
+def batch_specs(n_fits: int = 256, seed: int = SEED_BASE ^ (3 << 32)) -> list:
+    """A batch of independent fits: N uniform over {32, 64, 128, 256}, M
+    log-uniform in [1e4, 1e6], K uniform over {2, 3}, and 0 to 3 holes (the
+    first h of 10, 20 and 35 degrees), each fit with its own seed."""
+    u = SplitMix64(seed).stream(1).uniform(4 * n_fits).reshape(n_fits, 4)
+    specs = []
+    for i in range(n_fits):
+        N = BATCH_N[min(int(u[i, 0] * 4), 3)]
+        M = int(round(10.0 ** (4.0 + 2.0 * u[i, 1])))
+        K = 2 + min(int(u[i, 2] * 2), 1)
+        h = min(int(u[i, 3] * 4), 3)
+        specs.append(FitSpec(i, N, K, M, HOLES_DEG[:h], (seed ^ (i + 1)) & 0xFFFFFFFFFFFFFFFF))
+    return specs
+
+
+def serving_trace(rate_per_s: float, n_requests: int, seed: int = SEED_BASE ^ (4 << 32)) -> list:
+    """Requests arriving as a Poisson process of rate rate_per_s (exponential
+    gaps): N from {64, 128, 256, 512, 1024} with probabilities
+    {0.30, 0.30, 0.20, 0.15, 0.05}, M log-uniform in [5e4, 1.6e7], K = 3, the
+    three holes of the benchmark workload."""
+    rng = SplitMix64(seed)
+    gaps = -np.log(1.0 - rng.stream(1).uniform(n_requests)) / rate_per_s
+    t = np.cumsum(gaps)
+    un = rng.stream(2).uniform(n_requests)
+    um = rng.stream(3).uniform(n_requests)
+    cum = np.cumsum(SERVE_P)
+    specs = []
+    for i in range(n_requests):
+        N = SERVE_N[min(int(np.searchsorted(cum, un[i], side="right")), len(SERVE_N) - 1)]
+        M = int(round(5e4 * (1.6e7 / 5e4) ** um[i]))
+        specs.append(FitSpec(i, N, 3, M, HOLES_DEG, (seed ^ (i + 1)) & 0xFFFFFFFFFFFFFFFF, float(t[i])))
+    return specs
+
+
+def fit_workload(spec: FitSpec, xp=np, device=None, L_field: int = 200, noise: float = 1e-4) -> Workload:
+    """The nodes and values of one fit: track/hole nodes with the spec's holes
+    and a random field to degree L_field (degree power (1+l)^-3), noise sigma."""
+    x, meta = track_hole_nodes(spec.seed, spec.M, hole_deg=spec.holes_deg)
+    truth = random_field_coeffs(spec.seed, L_field)
+    if xp is np:
+        f = synth_field(truth, x, np, chunk=1 << 16)
+    else:
+        tx = xp.as_tensor(x, dtype=xp.float64, device=device)
+        f = synth_field(truth, tx, xp, chunk=1 << 22).cpu().numpy()
+    f = f + SplitMix64(spec.seed).stream(13).normal(len(f)) * noise
+    return Workload(f"fit{spec.index}_n{spec.N}_k{spec.K}_m{spec.M}", spec.N, spec.K, spec.M, x, f, truth, meta)
