@@ -125,9 +125,34 @@ hamls_status hamls_plan(hamls_plan_t* out, const double* nodes_xyz, const double
                         int64_t M, int N, int K, const hamls_params* p, cudaStream_t stream);
 
 /*
+ * hamls_plan_footprint - device memory that hamls_plan(M, N, K, p) would
+ * allocate, in bytes, without touching the device: the plan's arena exactly
+ * and the Shepard operator (sized only at plan time, after its members are
+ * counted) estimated with a quarter of slack. A refit operator
+ * (hamls_refit_prepare) is not included. For admission by memory footprint
+ * in a serving loop. Returns HAMLS_ERR_INVALID_ARG for shapes hamls_plan
+ * rejects.
+ */
+hamls_status hamls_plan_footprint(int64_t M, int N, int K, const hamls_params* p, size_t* bytes);
+
+/*
+ * hamls_plan_reserve - a plan for up to `capacity` nodes at bandwidth N and
+ * degree K without nodes yet: allocates what hamls_plan allocates for M =
+ * capacity and builds the node-independent part (quadrature grid, auxiliary
+ * grid, Shepard operator), waiting for `stream` once; hamls_replan then gives
+ * it nodes (fits, refits and Voronoi calls return HAMLS_ERR_INVALID_ARG until
+ * then). For pools of plans created ahead of a stream of fits.
+ * Returns as hamls_plan.
+ */
+hamls_status hamls_plan_reserve(hamls_plan_t* out, int64_t capacity, int N, int K, const hamls_params* p,
+                                cudaStream_t stream);
+
+/*
  * hamls_replan - rebuild the node-dependent part of an existing plan for a new
  * node set of M' <= M (the plan's capacity) nodes, with no allocation.
  * Arguments as in hamls_plan. Returns HAMLS_ERR_CAPACITY if M' is too large.
+ * The cell structure over the nodes is chosen from M' alone, so a fit gives
+ * the same coefficients in every plan that can hold its nodes.
  */
 hamls_status hamls_replan(hamls_plan_t plan, const double* nodes_xyz, const double* node_weights,
                           int64_t M, cudaStream_t stream);
@@ -201,6 +226,19 @@ hamls_status hamls_voronoi_weights(hamls_plan_t plan, cudaStream_t stream);
  * return the first device-detected error, or HAMLS_OK. Clears the status. */
 hamls_status hamls_sync(hamls_plan_t plan, int timeout_ms);
 
+/*
+ * hamls_status_async - the device status word without a host wait: enqueue on
+ * `stream` a copy of the plan's status word (the conditions hamls_sync would
+ * report, as bit flags) into *flags and clear the word on the device. *flags
+ * may be device memory or host memory (pinned for an asynchronous copy); it
+ * is valid once the stream has reached the copy. Called after each fit, it
+ * gives every fit its own status even when the plan is replanned before the
+ * host looks. hamls_status_from_flags maps a word to the status hamls_sync
+ * would return for it.
+ */
+hamls_status hamls_status_async(hamls_plan_t plan, uint32_t* flags, cudaStream_t stream);
+hamls_status hamls_status_from_flags(uint32_t flags);
+
 /* Statistics of the last plan/replan and fit (synchronises the stream); the
  * n(q) figures (sum_n, min_n, max_n, n_guarded) come from the last fit. */
 hamls_status hamls_stats(hamls_plan_t plan, hamls_fit_stats* out);
@@ -242,8 +280,11 @@ int64_t hamls_launch_count(hamls_plan_t plan, int reset);
  * The first call on a device looks up that array's device address (once per
  * device); make that first call before any stream capture. All calls share
  * the one array, so calls that overlap on the GPU (other streams, other host
- * threads) race: serialise them. Nodes that are not unit vectors are filed in
- * the north-pole cell; no status is reported for them.
+ * threads) race: serialise them. `stream` must belong to the current device
+ * (else HAMLS_ERR_INVALID_ARG). A CUDA error left pending by earlier work of
+ * the caller is reported as HAMLS_ERR_CUDA before anything is launched and is
+ * left pending. Nodes that are not unit vectors are filed in the north-pole
+ * cell; no status is reported for them.
  */
 hamls_status hamls_cells_noalloc(const double* nodes_xyz, int64_t M, int bands, int cells, uint32_t* keys_sorted,
                                  uint32_t* perm, uint32_t* cell_start, cudaStream_t stream);

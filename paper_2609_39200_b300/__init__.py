@@ -60,12 +60,16 @@ _SIGS = {
     "hamls_default_params": (None, [ctypes.POINTER(Params)]),
     "hamls_plan": (_I, [ctypes.POINTER(_P), _P, _P, _I64, _I, _I, ctypes.POINTER(Params), _P]),
     "hamls_replan": (_I, [_P, _P, _P, _I64, _P]),
+    "hamls_plan_reserve": (_I, [ctypes.POINTER(_P), _I64, _I, _I, ctypes.POINTER(Params), _P]),
+    "hamls_plan_footprint": (_I, [_I64, _I, _I, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]),
     "hamls_fit": (_I, [_P, _P, _P, _P]),
     "hamls_refit_prepare": (_I, [_P, _P]),
     "hamls_refit": (_I, [_P, _P, _P, _P]),
     "hamls_voronoi_areas": (_I, [_P, _P, _P]),
     "hamls_voronoi_weights": (_I, [_P, _P]),
     "hamls_sync": (_I, [_P, _I]),
+    "hamls_status_async": (_I, [_P, _P, _P]),
+    "hamls_status_from_flags": (_I, [ctypes.c_uint32]),
     "hamls_stats": (_I, [_P, ctypes.POINTER(FitStats)]),
     "hamls_destroy": (_I, [_P]),
     "hamls_status_string": (ctypes.c_char_p, [_I]),
@@ -142,14 +146,23 @@ class Plan:
     """A HAMLS plan: nodes x_i (M x 3 float64 unit vectors), bandwidth N, degree K."""
 
     def __init__(self, nodes, N: int, K: int, weights=None, params: Optional[Params] = None, stream=None,
-                 **kw):
+                 capacity: Optional[int] = None, **kw):
+        """A plan for ``nodes`` (hamls_plan); with nodes=None, a plan reserved
+        for up to ``capacity`` nodes that a replan fills (hamls_plan_reserve)."""
         self.N, self.K = int(N), int(K)
         self.params = params if params is not None else default_params(**kw)
-        self.M = int(nodes.shape[0])
-        self._keep = (nodes, weights)
         h = ctypes.c_void_p()
-        _check(lib().hamls_plan(ctypes.byref(h), _ptr(nodes), _ptr(weights), self.M, self.N, self.K,
-                                ctypes.byref(self.params), _stream(stream)), "hamls_plan")
+        if nodes is None:
+            self.M, self.capacity = 0, int(capacity)
+            self._keep = None
+            _check(lib().hamls_plan_reserve(ctypes.byref(h), self.capacity, self.N, self.K,
+                                            ctypes.byref(self.params), _stream(stream)), "hamls_plan_reserve")
+        else:
+            self.M = int(nodes.shape[0])
+            self.capacity = self.M
+            self._keep = (nodes, weights)
+            _check(lib().hamls_plan(ctypes.byref(h), _ptr(nodes), _ptr(weights), self.M, self.N, self.K,
+                                    ctypes.byref(self.params), _stream(stream)), "hamls_plan")
         self.h = h
 
     @property
@@ -197,6 +210,13 @@ class Plan:
     def voronoi_weights(self, stream=None):
         """Use the Voronoi areas of the current nodes as the weights v_i."""
         _check(lib().hamls_voronoi_weights(self.h, _stream(stream)), "hamls_voronoi_weights")
+
+    def status_async(self, flags, stream=None):
+        """Enqueue a copy of the device status word into ``flags`` (a uint32
+        slot: an int32 tensor element on the device or in pinned host memory)
+        and clear it; read it once the stream has passed this point and map
+        it with ``status_from_flags``."""
+        _check(lib().hamls_status_async(self.h, _ptr(flags), _stream(stream)), "hamls_status_async")
 
     def sync(self, timeout_ms: int = -1):
         _check(lib().hamls_sync(self.h, int(timeout_ms)), "hamls_sync")
@@ -300,6 +320,20 @@ def cells_noalloc(nodes: torch.Tensor, bands: int, cells: int, keys_sorted: torc
     all arguments are caller-owned device tensors (int32 views of uint32)."""
     _check(lib().hamls_cells_noalloc(_ptr(nodes), int(nodes.shape[0]), int(bands), int(cells), _ptr(keys_sorted),
                                      _ptr(perm), _ptr(cell_start), _stream(stream)), "hamls_cells_noalloc")
+
+
+def plan_footprint(M: int, N: int, K: int, params: Optional[Params] = None, **kw) -> int:
+    """Device bytes a plan for (M, N, K) would allocate (hamls_plan_footprint)."""
+    p = params if params is not None else default_params(**kw)
+    b = ctypes.c_size_t()
+    _check(lib().hamls_plan_footprint(int(M), int(N), int(K), ctypes.byref(p), ctypes.byref(b)),
+           "hamls_plan_footprint")
+    return int(b.value)
+
+
+def status_from_flags(flags: int) -> int:
+    """The hamls_status (0 = ok) for a status word from Plan.status_async."""
+    return int(lib().hamls_status_from_flags(int(flags) & 0xFFFFFFFF))
 
 
 def to_complex(coeffs: torch.Tensor) -> np.ndarray:

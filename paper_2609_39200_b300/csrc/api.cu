@@ -82,8 +82,9 @@ struct hamls_plan_s {
   bool mixed = false, has_weights = false;
   Arena arena;
   GridTables g;
-  // scattered nodes
-  int B = 0, P = 0;
+  // scattered nodes: the cell structure (B bands, P cells per band) follows
+  // the current node count; Bcap is the largest one the arena holds
+  int B = 0, P = 0, Bcap = 0, edge_B = 0;
   uint32_t *keys, *vals, *keys_alt, *vals_alt, *counts, *start;
   float4 *edge, *aedge;            // band-edge tables of the node and auxiliary cells
   const uint32_t *perm = nullptr, *skeys = nullptr;
@@ -183,8 +184,8 @@ void carve(hamls_plan_s* P) {
   P->keys_alt = A.take<uint32_t>(M);
   P->vals_alt = A.take<uint32_t>(M);
   P->counts = A.take<uint32_t>((size_t)256 * radix_blocks(sortmax) + scan_partials(sortmax));
-  P->start = A.take<uint32_t>((size_t)P->B * P->P + 1);
-  P->edge = A.take<float4>((size_t)P->B + 1);
+  P->start = A.take<uint32_t>((size_t)P->Bcap * 2 * P->Bcap + 1);
+  P->edge = A.take<float4>((size_t)P->Bcap + 1);
   P->aedge = A.take<float4>((size_t)P->aB + 1);
   P->px = A.take<double>(M);
   P->py = A.take<double>(M);
@@ -321,6 +322,14 @@ SupportArgs support_args(hamls_plan_s* P) {
 // node-dependent part of the plan (Sec. 2.2: cell list, d_n, delta, n(q))
 hamls_status build_nodes(hamls_plan_s* P, const double* nodes, const double* wts, int64_t M, cudaStream_t s) {
   P->M = M;
+  // the cell structure depends on M alone (not on the capacity), so a fit
+  // gives the same result in any plan that holds its nodes
+  P->B = key_bands(M);
+  P->P = 2 * P->B;
+  if (P->edge_B != P->B) {
+    build_edge_table(P->B, P->edge, s, &P->launches);
+    P->edge_B = P->B;
+  }
   P->op_valid = false;   // a refit operator belongs to the nodes it was built for
   P->has_weights = wts != nullptr;
   reset_status_kernel<<<1, 32, 0, s>>>(P->st, 1);
@@ -378,7 +387,6 @@ hamls_status build_nodes(hamls_plan_s* P, const double* nodes, const double* wts
 
 hamls_status build_static(hamls_plan_s* P, cudaStream_t s) {
   build_grid_tables(P->g, P->mixed, !P->mixed, s, &P->launches);
-  build_edge_table(P->B, P->edge, s, &P->launches);
   build_edge_table(P->aB, P->aedge, s, &P->launches);
   fibonacci_points(P->ax, P->ay, P->az, P->M_aux, s, &P->launches);
   CellBuild cb;
@@ -481,20 +489,13 @@ const char* hamls_status_string(hamls_status s) {
   return "unknown status";
 }
 
-hamls_status hamls_plan(hamls_plan_t* out, const double* nodes_xyz, const double* node_weights, int64_t M,
-                        int N, int K, const hamls_params* pin, cudaStream_t stream) {
-  if (!out) return HAMLS_ERR_INVALID_ARG;
-  *out = nullptr;
-  hamls_params p;
-  if (pin) p = *pin;
-  else hamls_default_params(&p);
-  if (!nodes_xyz || K < 1 || K > KMAX || N < 1 || N > 1024 || !validate_params(p)) return HAMLS_ERR_INVALID_ARG;
+// shape of a plan for (M, N, K, p): every size the arena depends on
+static hamls_status plan_shape(hamls_plan_s* P, int64_t M, int N, int K, const hamls_params& p) {
+  if (K < 1 || K > KMAX || N < 1 || N > 1024 || !validate_params(p)) return HAMLS_ERR_INVALID_ARG;
   const int m = dim_tan_host(K);
   const int n_target = p.n_target > 0 ? p.n_target : 4 * m;
   if (n_target > KNN_MAX || n_target < m) return HAMLS_ERR_INVALID_ARG;
   if (M < n_target || M >= (int64_t)1 << 31) return HAMLS_ERR_INVALID_ARG;
-  hamls_plan_s* P = new (std::nothrow) hamls_plan_s();
-  if (!P) return HAMLS_ERR_OOM;
   P->p = p;
   P->mixed = p.precision == HAMLS_MIXED;
   P->Mcap = M;
@@ -507,14 +508,54 @@ hamls_status hamls_plan(hamls_plan_t* out, const double* nodes_xyz, const double
   P->M_aux = (int)(p.aux_points > 0 ? p.aux_points : 2 * (int64_t)P->MQ);
   P->g.N = N;
   P->g.hc = N / 2 + 1;
-  P->B = key_bands(M);
+  P->Bcap = key_bands(M);
+  P->B = P->Bcap;
   P->P = 2 * P->B;
   P->aB = key_bands(P->M_aux);
   P->aP = 2 * P->aB;
   factor_radices(P->L, P->radices, P->nrad);
-  if (P->nrad > 32) {
-    delete P;
-    return HAMLS_ERR_INVALID_ARG;
+  if (P->nrad > 32) return HAMLS_ERR_INVALID_ARG;
+  return HAMLS_OK;
+}
+
+hamls_status hamls_plan_footprint(int64_t M, int N, int K, const hamls_params* pin, size_t* bytes) {
+  if (!bytes) return HAMLS_ERR_INVALID_ARG;
+  *bytes = 0;
+  hamls_params p;
+  if (pin) p = *pin;
+  else hamls_default_params(&p);
+  hamls_plan_s* P = new (std::nothrow) hamls_plan_s();
+  if (!P) return HAMLS_ERR_OOM;
+  hamls_status r = plan_shape(P, M, N, K, p);
+  if (r == HAMLS_OK) {
+    carve(P);   // measure only (no base address)
+    // the Shepard operator: about pi (aux_radius)^2 auxiliary points per grid
+    // node (a cap of radius aux_radius spacings), 4 B index + weight each,
+    // with a quarter of slack, plus one weight sum per grid node
+    const double wsz = P->mixed ? 4.0 : 8.0;
+    const double per = 1.25 * M_PI * p.aux_radius * p.aux_radius + 4.0;
+    *bytes = P->arena.off + (size_t)((double)P->MQ * (per * (4.0 + wsz) + wsz)) + sizeof(DevStatus);
+  }
+  delete P;
+  return r;
+}
+
+hamls_status hamls_plan(hamls_plan_t* out, const double* nodes_xyz, const double* node_weights, int64_t M,
+                        int N, int K, const hamls_params* pin, cudaStream_t stream) {
+  if (!out) return HAMLS_ERR_INVALID_ARG;
+  *out = nullptr;
+  hamls_params p;
+  if (pin) p = *pin;
+  else hamls_default_params(&p);
+  if (!nodes_xyz) return HAMLS_ERR_INVALID_ARG;
+  hamls_plan_s* P = new (std::nothrow) hamls_plan_s();
+  if (!P) return HAMLS_ERR_OOM;
+  {
+    const hamls_status r = plan_shape(P, M, N, K, p);
+    if (r != HAMLS_OK) {
+      delete P;
+      return r;
+    }
   }
   cudaGetDevice(&P->device);
   cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
@@ -540,6 +581,50 @@ hamls_status hamls_plan(hamls_plan_t* out, const double* nodes_xyz, const double
     hamls_destroy(P);
     return s;
   }
+  *out = P;
+  return HAMLS_OK;
+}
+
+hamls_status hamls_plan_reserve(hamls_plan_t* out, int64_t capacity, int N, int K, const hamls_params* pin,
+                                cudaStream_t stream) {
+  if (!out) return HAMLS_ERR_INVALID_ARG;
+  *out = nullptr;
+  hamls_params p;
+  if (pin) p = *pin;
+  else hamls_default_params(&p);
+  hamls_plan_s* P = new (std::nothrow) hamls_plan_s();
+  if (!P) return HAMLS_ERR_OOM;
+  hamls_status r = plan_shape(P, capacity, N, K, p);
+  if (r != HAMLS_OK) {
+    delete P;
+    return r;
+  }
+  cudaGetDevice(&P->device);
+  cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+  carve(P);
+  P->arena.cap = P->arena.off;
+  if (cudaMalloc((void**)&P->arena.base, P->arena.cap) != cudaSuccess) {
+    cudaGetLastError();
+    delete P;
+    return HAMLS_ERR_OOM;
+  }
+  carve(P);
+  if (cudaMallocHost((void**)&P->st_host, sizeof(DevStatus)) != cudaSuccess) {
+    cudaFree(P->arena.base);
+    delete P;
+    return HAMLS_ERR_OOM;
+  }
+  for (int i = 0; i < NSTAGE; ++i) P->ev_used[i] = false;
+  P->M = 0;   // no nodes until hamls_replan
+  reset_status_kernel<<<1, 32, 0, stream>>>(P->st, 1);
+  ++P->launches;
+  r = build_static(P, stream);
+  if (r == HAMLS_OK) r = cuda_status(cudaStreamSynchronize(stream));
+  if (r != HAMLS_OK) {
+    hamls_destroy(P);
+    return r;
+  }
+  P->last = stream;
   *out = P;
   return HAMLS_OK;
 }
@@ -631,6 +716,7 @@ static hamls_status run_step3(hamls_plan_s* P, double* coeffs, cudaStream_t s) {
 
 hamls_status hamls_fit(hamls_plan_t P, const double* values, double* coeffs, cudaStream_t s) {
   if (!P || !values || !coeffs) return HAMLS_ERR_INVALID_ARG;
+  if (P->M <= 0) return HAMLS_ERR_INVALID_ARG;   // a reserved plan without nodes
   reset_status_kernel<<<1, 32, 0, s>>>(P->st, 0);
   ++P->launches;
   const double* dv = values;
@@ -647,6 +733,7 @@ hamls_status hamls_fit(hamls_plan_t P, const double* values, double* coeffs, cud
 
 hamls_status hamls_refit_prepare(hamls_plan_t P, cudaStream_t s) {
   if (!P) return HAMLS_ERR_INVALID_ARG;
+  if (P->M <= 0) return HAMLS_ERR_INVALID_ARG;   // a reserved plan without nodes
   P->op_valid = false;
   // a fit with zero values: the Gram moments, n(q) and the guard for the nodes
   reset_status_kernel<<<1, 32, 0, s>>>(P->st, 0);
@@ -716,6 +803,7 @@ static float4* vor_scratch(hamls_plan_s* P) { return reinterpret_cast<float4*>(P
 
 hamls_status hamls_voronoi_areas(hamls_plan_t P, double* areas, cudaStream_t s) {
   if (!P || !areas) return HAMLS_ERR_INVALID_ARG;
+  if (P->M <= 0) return HAMLS_ERR_INVALID_ARG;   // a reserved plan without nodes
   const bool dev = is_device_ptr(areas);
   double* dst = dev ? areas : P->in_vals;
   stage_begin(P, 8, s);
@@ -728,6 +816,7 @@ hamls_status hamls_voronoi_areas(hamls_plan_t P, double* areas, cudaStream_t s) 
 
 hamls_status hamls_voronoi_weights(hamls_plan_t P, cudaStream_t s) {
   if (!P) return HAMLS_ERR_INVALID_ARG;
+  if (P->M <= 0) return HAMLS_ERR_INVALID_ARG;   // a reserved plan without nodes
   stage_begin(P, 8, s);
   run_voronoi(node_cells(P), P->mixed, vor_scratch(P), nullptr, P->sw, P->swf, P->st, s, &P->launches);
   stage_end(P, 8, s);
@@ -754,11 +843,23 @@ hamls_status hamls_sync(hamls_plan_t P, int timeout_ms) {
   }
   unsigned f = P->st_host->flags;
   if (f) HAMLS_TRY(cudaMemsetAsync(&P->st->flags, 0, sizeof(unsigned), s));
+  return hamls_status_from_flags(f);
+}
+
+hamls_status hamls_status_from_flags(uint32_t f) {
   if (f & ST_BADNODE) return HAMLS_ERR_INVALID_ARG;
   if (f & ST_NONFINITE) return HAMLS_ERR_NONFINITE;
   if (f & ST_SUPPORT) return HAMLS_ERR_SUPPORT_TOO_LARGE;
   if (f & (ST_UNDERDET | ST_KNN)) return HAMLS_ERR_UNDERDETERMINED;
   if (f & ST_VORONOI) return HAMLS_ERR_VORONOI;
+  return HAMLS_OK;
+}
+
+hamls_status hamls_status_async(hamls_plan_t P, uint32_t* flags, cudaStream_t s) {
+  if (!P || !flags) return HAMLS_ERR_INVALID_ARG;
+  HAMLS_TRY(cudaMemcpyAsync(flags, &P->st->flags, sizeof(uint32_t), cudaMemcpyDefault, s));
+  HAMLS_TRY(cudaMemsetAsync(&P->st->flags, 0, sizeof(uint32_t), s));
+  P->last = s;
   return HAMLS_OK;
 }
 

@@ -16,6 +16,27 @@
 
 namespace hamls {
 
+int current_sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess || n < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n;
+}
+
+// done_mask: one bit per device (devices 0..31; others set the attribute on
+// every call). Setting it twice is harmless, so a race only repeats the call.
+void set_smem_attr_once(const void* func, int bytes, unsigned* done_mask) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned bit = dev < 32 ? 1u << dev : 0u;
+  if (bit && (__atomic_load_n(done_mask, __ATOMIC_ACQUIRE) & bit)) return;
+  cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (bit) __atomic_fetch_or(done_mask, bit, __ATOMIC_ACQ_REL);
+}
+
 // P_n and D_n = P_n - P_{n-1} at t = cos(theta) = 1 - u, u = 2 sin^2(theta/2),
 // by the three-term recurrence rewritten on differences:
 //   D_{k+1} = (k D_k - (2k+1) u P_k) / (k+1),  P_{k+1} = P_k + D_{k+1},

@@ -6,6 +6,11 @@
 
 namespace hamls {
 
+// SM count of the current device (grid sizing); set_smem_attr raises a
+// kernel's dynamic shared-memory limit once per device (thread-safe)
+int current_sm_count();
+void set_smem_attr_once(const void* func, int bytes, unsigned* done_mask);
+
 // ------------------------------------------------------------------ cells.cu
 struct CellBuild {
   int n, B, P;

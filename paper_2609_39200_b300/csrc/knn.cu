@@ -696,7 +696,7 @@ static double aux_radius2(const SupportArgs& a) {
 void shepard_rows(const SupportArgs& a, uint32_t* rows, uint32_t* col, void* w, void* sw, bool fill,
                   cudaStream_t s, int64_t* launches) {
   const int MQ = (a.N + 1) * (2 * a.N + 2);
-  const int blocks = grid_for(MQ, 4, 148 * 16);
+  const int blocks = grid_for(MQ, 4, a.num_sms * 16);
   const double r2 = aux_radius2(a);
   if (a.fp64) {
     if (fill)
@@ -730,7 +730,7 @@ void run_guard(const SupportArgs& a, cudaStream_t s, int64_t* launches) {
 void run_knn_queries(const Cells& nodes, const double* q, int64_t nq, int n, double* c2_out, DevStatus* st,
                      cudaStream_t s, int64_t* launches) {
   if (nq <= 0) return;
-  const int blocks = grid_for((int)nq, KNN_WARPS, 148 * 16);
+  const int blocks = grid_for((int)nq, KNN_WARPS, current_sm_count() * 16);
   if (n <= 48)
     knn_query_kernel<12><<<blocks, KNN_WARPS * 32, 0, s>>>(nodes, q, nq, n, initial_radius(n, nodes.n), c2_out, st);
   else
@@ -784,7 +784,7 @@ __global__ void __launch_bounds__(128) ball_query_kernel(Cells g, const double* 
 void run_ball_queries(const Cells& nodes, const double* q, const double* rho2, int64_t nq, int64_t* count,
                       int64_t* idsum, uint64_t* idhash, cudaStream_t s, int64_t* launches) {
   if (nq <= 0) return;
-  ball_query_kernel<<<grid_for((int)nq, 4, 148 * 16), 128, 0, s>>>(nodes, q, rho2, nq, count, idsum, idhash);
+  ball_query_kernel<<<grid_for((int)nq, 4, current_sm_count() * 16), 128, 0, s>>>(nodes, q, rho2, nq, count, idsum, idhash);
   ++*launches;
 }
 

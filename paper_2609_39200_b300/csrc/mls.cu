@@ -756,7 +756,7 @@ __global__ void to_float_kernel(const double* __restrict__ y, int n, float* __re
 template <int K, bool MIXED>
 static void launch_op(const MlsArgs& a, const SolveParams& P, int part, double* gamma, uint32_t* rows, uint32_t* col,
                       void* val, unsigned long long* total, cudaStream_t s, int64_t* launches) {
-  const int wblocks = (a.MQ + 3) / 4 < 148 * 64 ? (a.MQ + 3) / 4 : 148 * 64;
+  const int wblocks = (a.MQ + 3) / 4 < a.num_sms * 64 ? (a.MQ + 3) / 4 : a.num_sms * 64;
   if (part == 0) {
     op_rows_kernel<K, MIXED, false><<<wblocks, 128, 0, s>>>(a, gamma, rows, col, val, total);
     ++*launches;
@@ -789,7 +789,8 @@ void run_refit_operator(const MlsArgs& a, bool mixed, int part, double* gamma, u
 
 void run_refit_apply(int MQ, bool mixed, const uint32_t* rows, const uint32_t* col, const void* val,
                      const double* y, int M, float* yf, double* f, DevStatus* st, cudaStream_t s, int64_t* launches) {
-  const int blocks = (MQ + 7) / 8 < 148 * 64 ? (MQ + 7) / 8 : 148 * 64;
+  const int cap = current_sm_count() * 64;
+  const int blocks = (MQ + 7) / 8 < cap ? (MQ + 7) / 8 : cap;
   if (mixed) {
     to_float_kernel<<<(M + 255) / 256, 256, 0, s>>>(y, M, yf);
     op_apply_kernel<float><<<blocks, 256, 0, s>>>(MQ, rows, col, reinterpret_cast<const float*>(val), yf, f, st);

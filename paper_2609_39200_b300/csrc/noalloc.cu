@@ -71,16 +71,27 @@ extern "C" hamls_status hamls_cells_noalloc(const double* nodes_xyz, int64_t M, 
   }
   const int n = (int)M;
   if ((int64_t)256 * radix_blocks(n) + scan_partials(n) > NOALLOC_COUNT_WORDS) return HAMLS_ERR_CAPACITY;
+  // the scratch belongs to the current device: the stream must too
+  int sdev = -1;
+  if (cudaStreamGetDevice(stream, &sdev) != cudaSuccess) {
+    cudaGetLastError();
+    return HAMLS_ERR_INVALID_ARG;
+  }
+  if (sdev != dev) return HAMLS_ERR_INVALID_ARG;
+  // an error the caller left pending is the caller's: report it without
+  // clearing it and launch nothing, so that the checks below see only this
+  // call's launches
+  if (cudaPeekAtLastError() != cudaSuccess) return HAMLS_ERR_CUDA;
   uint32_t* keys_alt = scratch;
   uint32_t* vals_alt = scratch + NOALLOC_MAX_M;
   uint32_t* counts = scratch + 2 * NOALLOC_MAX_M;
   DevStatus* st = reinterpret_cast<DevStatus*>(scratch + 2 * NOALLOC_MAX_M + NOALLOC_COUNT_WORDS);
-  cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), stream);
-  if (e != cudaSuccess) return HAMLS_ERR_CUDA;
+  if (cudaMemsetAsync(st, 0, sizeof(DevStatus), stream) != cudaSuccess) return HAMLS_ERR_CUDA;
   int bits = 0;
   while ((1ull << bits) < (unsigned long long)bands * cells) ++bits;
   const int passes = (bits + 7) / 8;
-  // start where an odd number of ping-pong passes ends in the caller's arrays
+  // start where the ping-pong passes end in the caller's arrays (an odd
+  // count starts in the scratch, an even one in the caller's arrays)
   uint32_t *k0 = keys_sorted, *v0 = perm, *k1 = keys_alt, *v1 = vals_alt;
   if (passes & 1) {
     k0 = keys_alt;
@@ -90,8 +101,9 @@ extern "C" hamls_status hamls_cells_noalloc(const double* nodes_xyz, int64_t M, 
   }
   int64_t launches = 0;
   launch_cell_keys(nodes_xyz, n, bands, cells, k0, v0, st, stream);
+  if (cudaGetLastError() != cudaSuccess) return HAMLS_ERR_CUDA;
   radix_sort_pairs(k0, v0, k1, v1, n, bits, counts, stream, &launches);
+  if (cudaGetLastError() != cudaSuccess) return HAMLS_ERR_CUDA;
   launch_csr(keys_sorted, n, bands * cells, cell_start, stream);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? HAMLS_OK : HAMLS_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? HAMLS_OK : HAMLS_ERR_CUDA;
 }

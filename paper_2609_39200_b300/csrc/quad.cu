@@ -166,12 +166,9 @@ static void launch_quad(const QuadArgs& a, const typename C2<T>::t* W, const T* 
   const int N = a.g->N, L = 2 * N + 2, hc = a.g->hc;
   const size_t smem_fft = 2 * (size_t)L * sizeof(cT);
   const size_t smem_leg = 2 * (size_t)hc * sizeof(cT);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(ring_fft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(legendre_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  static unsigned done_fft = 0, done_leg = 0;   // per device
+  set_smem_attr_once((const void*)ring_fft_kernel<T>, 200 * 1024, &done_fft);
+  set_smem_attr_once((const void*)legendre_kernel<T>, 200 * 1024, &done_leg);
   if (part & 1) {
     ring_fft_kernel<T><<<(N + 2) / 2, 256, smem_fft, s>>>(a.fgrid, N, a, W, reinterpret_cast<cT*>(a.F));
     ++*launches;
