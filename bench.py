@@ -555,8 +555,7 @@ def run_ours(args):
                 "clocks": clk.summary(), "fp64_form": fp64, "refit": refit, "voronoi": voronoi, "l2_error": l2,
                 "mls_stats": {k: stats[k] for k in ("sum_n", "min_n", "max_n", "n_regularized", "n_guarded",
                                                     "n_fp64_redo", "n_dropped")},
-                "knn_stats": {k: stats[k] for k in ("aux_points", "knn_candidates", "knn_scans",
-                                                    "knn_exact_fallbacks")}}
+                "knn_stats": {k: stats[k] for k in stats if k.startswith("knn_") or k == "aux_points"}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
