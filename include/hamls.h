@@ -170,6 +170,27 @@ hamls_status hamls_replan(hamls_plan_t plan, const double* nodes_xyz, const doub
 hamls_status hamls_fit(hamls_plan_t plan, const double* values, double* coeffs, cudaStream_t stream);
 
 /*
+ * hamls_quadrature_batch - Algorithm 1 step 3 for B sets of grid values at
+ * once (eq. quadrature_based_approximation): for value sets that share the
+ * bandwidth N (refits of many value series, or fits of different plans of
+ * the same N), the Legendre quadrature of all sets is one matrix product per
+ * order m and parity, which MIXED plans run on the tensor cores (tcgen05,
+ * 3xTF32 products with FP32 accumulation; relative error ~1e-6, as the FP32
+ * contraction of hamls_fit). FP64 plans run the FP64 contraction set by set.
+ *   fgrid   B x M_Q doubles (device): set b at b M_Q, grid nodes ring-major
+ *           (k (2N+2) + j), e.g. the grid values of hamls_debug_grid
+ *   coeffs  B x (N+1)(N+2)/2 complex (device), each set packed as hamls_fit
+ *   B       1 <= B <= 65535
+ * The first call with a given B allocates the workspace (spectra and folded
+ * spectra, about B (N+1)^2 16 B; owned by the plan, reused by later calls of
+ * B or fewer sets) and, when it grows, waits for the plan's stream. A tile
+ * whose copies or products did not arrive within about 2 s is reported by
+ * hamls_sync as HAMLS_ERR_TIMEOUT.
+ */
+hamls_status hamls_quadrature_batch(hamls_plan_t plan, const double* fgrid, double* coeffs, int B,
+                                    cudaStream_t stream);
+
+/*
  * Values-only refits: new values at the same nodes (a time series on fixed
  * stations). For fixed nodes every grid value f(q_j) = M_y(q_j) is linear in
  * the data y: the Gram matrix, chi and tau~ of the local problem depend on the

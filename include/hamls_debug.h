@@ -54,6 +54,14 @@ hamls_status hamls_debug_quadrature(hamls_plan_t plan, const double* fgrid, doub
 /* Gauss-Legendre nodes t_k (descending) and weights w_k, N+1 each. */
 hamls_status hamls_debug_gl(hamls_plan_t plan, double* t, double* w, cudaStream_t stream);
 
+/* The tensor-core product used by the batched Legendre contraction, alone:
+ * C (M x N, row-major) = A (M x K) B (N x K)^T, all FP32 row-major device
+ * arrays, K a multiple of 4, computed as 3xTF32 on tcgen05 (FP32
+ * accumulation). Synchronises the stream; HAMLS_ERR_TIMEOUT if a tile gave
+ * up waiting for its copies or products. */
+hamls_status hamls_debug_tc_gemm(const float* A, const float* B, float* C, int M, int N, int K,
+                                 cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,6 +63,7 @@ _SIGS = {
     "hamls_plan_reserve": (_I, [ctypes.POINTER(_P), _I64, _I, _I, ctypes.POINTER(Params), _P]),
     "hamls_plan_footprint": (_I, [_I64, _I, _I, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]),
     "hamls_fit": (_I, [_P, _P, _P, _P]),
+    "hamls_quadrature_batch": (_I, [_P, _P, _P, _I, _P]),
     "hamls_refit_prepare": (_I, [_P, _P]),
     "hamls_refit": (_I, [_P, _P, _P, _P]),
     "hamls_voronoi_areas": (_I, [_P, _P, _P]),
@@ -84,6 +85,7 @@ _SIGS = {
     "hamls_debug_quadrature": (_I, [_P, _P, _P, _P]),
     "hamls_debug_gl": (_I, [_P, _P, _P, _P]),
     "hamls_cells_noalloc": (_I, [_P, _I64, _I, _I, _P, _P, _P, _P]),
+    "hamls_debug_tc_gemm": (_I, [_P, _P, _P, _I, _I, _I, _P]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -183,6 +185,17 @@ class Plan:
             out = torch.empty((n_coeffs(self.N), 2), dtype=torch.float64, device=dev)
         self._keep_fit = (values, out)
         _check(lib().hamls_fit(self.h, _ptr(values), _ptr(out), _stream(stream)), "hamls_fit")
+        return out
+
+    def quadrature_batch(self, fgrid, out=None, stream=None):
+        """Step 3 for B sets of grid values (B x M_Q float64 device tensor):
+        coefficients (B, ncoef, 2), on the tensor cores for mixed plans."""
+        B = int(fgrid.shape[0])
+        if out is None:
+            out = torch.empty((B, n_coeffs(self.N), 2), dtype=torch.float64, device=fgrid.device)
+        self._keep_qb = (fgrid, out)
+        _check(lib().hamls_quadrature_batch(self.h, _ptr(fgrid), _ptr(out), B, _stream(stream)),
+               "hamls_quadrature_batch")
         return out
 
     def refit_prepare(self, stream=None):
@@ -334,6 +347,16 @@ def plan_footprint(M: int, N: int, K: int, params: Optional[Params] = None, **kw
 def status_from_flags(flags: int) -> int:
     """The hamls_status (0 = ok) for a status word from Plan.status_async."""
     return int(lib().hamls_status_from_flags(int(flags) & 0xFFFFFFFF))
+
+
+def debug_tc_gemm(A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
+    """C = A B^T on the tensor cores (3xTF32, FP32 accumulation): A (M, K)
+    and B (N, K) contiguous float32 device tensors, K a multiple of 4."""
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.zeros((M, N), dtype=torch.float32, device=A.device)
+    _check(lib().hamls_debug_tc_gemm(_ptr(A), _ptr(B), _ptr(C), M, N, K, _stream(stream)), "hamls_debug_tc_gemm")
+    return C
 
 
 def to_complex(coeffs: torch.Tensor) -> np.ndarray:

@@ -61,6 +61,7 @@ __global__ void reset_status_kernel(DevStatus* st, int full) {
   if (threadIdx.x == 0) {
     if (full) {
       st->flags = 0;
+      st->tc_err = 0;
       for (int i = 0; i < 16; ++i) st->cnt[i] = 0;
       st->cnt[C_MIN_N] = ~0ull;
     } else {
@@ -81,7 +82,15 @@ struct hamls_plan_s {
   hamls_params p;
   bool mixed = false, has_weights = false;
   Arena arena;
-  GridTables g;
+  GridTables g;                    // pointers into the shared tables of (device, N, form)
+  SharedTables* tables = nullptr;
+  // batched step 3 (hamls_quadrature_batch): spectra and folded spectra of up
+  // to batch_cap value sets, allocated on first use and grown as needed
+  void* batch_mem = nullptr;
+  int batch_cap = 0;
+  float2* batch_F = nullptr;
+  float* batch_G = nullptr;
+  unsigned* batch_err = nullptr;
   // scattered nodes: the cell structure (B bands, P cells per band) follows
   // the current node count; Bcap is the largest one the arena holds
   int B = 0, P = 0, Bcap = 0, edge_B = 0;
@@ -162,22 +171,7 @@ void carve(hamls_plan_s* P) {
   const int N = P->N, L = P->L, MQ = P->MQ, Ma = P->M_aux;
   const size_t ncoef = (size_t)(N + 1) * (N + 2) / 2;
   const int sortmax = (int)std::max<int64_t>(std::max<int64_t>(M, Ma), MQ);
-  // grid tables
-  P->g.t = A.take<double>(N + 1);
-  P->g.w = A.take<double>(N + 1);
-  P->g.s = A.take<double>(N + 1);
-  P->g.cphi = A.take<double>(L);
-  P->g.sphi = A.take<double>(L);
-  P->g.a_rec = A.take<double>(ncoef);
-  P->g.b_rec = A.take<double>(ncoef);
-  P->g.A64 = P->mixed ? nullptr : A.take<double>(ncoef * P->g.hc);
-  P->g.A32 = P->mixed ? A.take<float>(ncoef * P->g.hc) : nullptr;
-  P->g.W64 = A.take<double2>(L);
-  P->g.W32 = A.take<float2>(L);
-  P->g.tf = A.take<float>(N + 1);
-  P->g.sf = A.take<float>(N + 1);
-  P->g.cpf = A.take<float>(L);
-  P->g.spf = A.take<float>(L);
+  // (the grid tables are shared across plans: tables.cu)
   // nodes
   P->keys = A.take<uint32_t>(M);
   P->vals = A.take<uint32_t>(M);
@@ -386,7 +380,10 @@ hamls_status build_nodes(hamls_plan_s* P, const double* nodes, const double* wts
 }
 
 hamls_status build_static(hamls_plan_s* P, cudaStream_t s) {
-  build_grid_tables(P->g, P->mixed, !P->mixed, s, &P->launches);
+  cudaError_t te = cudaSuccess;
+  P->tables = tables_acquire(P->N, P->mixed, s, &P->launches, &te);
+  if (!P->tables) return cuda_status(te == cudaSuccess ? cudaErrorMemoryAllocation : te);
+  P->g = P->tables->g;
   build_edge_table(P->aB, P->aedge, s, &P->launches);
   fibonacci_points(P->ax, P->ay, P->az, P->M_aux, s, &P->launches);
   CellBuild cb;
@@ -508,6 +505,7 @@ static hamls_status plan_shape(hamls_plan_s* P, int64_t M, int N, int K, const h
   P->M_aux = (int)(p.aux_points > 0 ? p.aux_points : 2 * (int64_t)P->MQ);
   P->g.N = N;
   P->g.hc = N / 2 + 1;
+  P->g.hcp = (P->g.hc + 7) / 8 * 8;
   P->Bcap = key_bands(M);
   P->B = P->Bcap;
   P->P = 2 * P->B;
@@ -534,7 +532,9 @@ hamls_status hamls_plan_footprint(int64_t M, int N, int K, const hamls_params* p
     // with a quarter of slack, plus one weight sum per grid node
     const double wsz = P->mixed ? 4.0 : 8.0;
     const double per = 1.25 * M_PI * p.aux_radius * p.aux_radius + 4.0;
-    *bytes = P->arena.off + (size_t)((double)P->MQ * (per * (4.0 + wsz) + wsz)) + sizeof(DevStatus);
+    // the grid tables count in full, as for the first plan of its (N, form)
+    *bytes = P->arena.off + (size_t)((double)P->MQ * (per * (4.0 + wsz) + wsz)) + sizeof(DevStatus) +
+             tables_bytes(N, P->mixed);
   }
   delete P;
   return r;
@@ -795,6 +795,57 @@ hamls_status hamls_refit(hamls_plan_t P, const double* values, double* coeffs, c
   return run_step3(P, coeffs, s);
 }
 
+hamls_status hamls_quadrature_batch(hamls_plan_t P, const double* fgrid, double* coeffs, int B, cudaStream_t s) {
+  if (!P || !fgrid || !coeffs || B < 1 || B > 65535) return HAMLS_ERR_INVALID_ARG;
+  if (!is_device_ptr(fgrid) || !is_device_ptr(coeffs)) return HAMLS_ERR_INVALID_ARG;
+  const int N = P->N;
+  const size_t ncoef = (size_t)(N + 1) * (N + 2) / 2;
+  if (!P->mixed) {
+    // the FP64 form: its own contraction per value set (the tensor cores
+    // carry FP32 accuracy only)
+    for (int b = 0; b < B; ++b) {
+      QuadArgs q;
+      memset(&q, 0, sizeof(q));
+      q.g = &P->g;
+      q.fgrid = fgrid + (size_t)b * P->MQ;
+      q.F = P->F;
+      q.coeffs = coeffs + (size_t)b * ncoef * 2;
+      for (int i = 0; i < P->nrad; ++i) q.radices[i] = P->radices[i];
+      q.nrad = P->nrad;
+      run_quadrature(q, false, s, &P->launches);
+    }
+    P->last = s;
+    return cuda_status(cudaGetLastError());
+  }
+  if (B > P->batch_cap) {
+    // workspace for B sets: spectra B (N+1)^2 complex FP32, folded spectra
+    // 2 (N+1) x 2B x hcp FP32, an error word
+    if (P->batch_mem) {
+      HAMLS_TRY(cudaStreamSynchronize(P->last));
+      cudaFree(P->batch_mem);
+      P->batch_mem = nullptr;
+      P->batch_cap = 0;
+    }
+    const size_t bF = ((size_t)B * (N + 1) * (N + 1) * sizeof(float2) + 255) & ~size_t(255);
+    const size_t bG = ((size_t)2 * (N + 1) * 2 * B * P->g.hcp * sizeof(float) + 255) & ~size_t(255);
+    HAMLS_TRY(cudaMalloc(&P->batch_mem, bF + bG + 256));
+    P->batch_F = reinterpret_cast<float2*>(P->batch_mem);
+    P->batch_G = reinterpret_cast<float*>(reinterpret_cast<char*>(P->batch_mem) + bF);
+    P->batch_err = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(P->batch_mem) + bF + bG);
+    P->batch_cap = B;
+  }
+  HAMLS_TRY(cudaMemsetAsync(P->batch_err, 0, sizeof(unsigned), s));
+  stage_begin(P, 6, s);
+  cudaError_t e = run_quadrature_batch(P->g, P->radices, P->nrad, fgrid, B, P->batch_F, P->batch_G,
+                                       P->tables->jobs, P->tables->njobs, coeffs, P->batch_err, s, &P->launches);
+  stage_end(P, 6, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  // a tile that gave up waiting is reported by hamls_sync
+  HAMLS_TRY(cudaMemcpyAsync(&P->st->tc_err, P->batch_err, sizeof(unsigned), cudaMemcpyDeviceToDevice, s));
+  P->last = s;
+  return cuda_status(cudaGetLastError());
+}
+
 // Voronoi areas of the plan's nodes (Sec. 2.2, after Theorem 2.1): into the
 // caller's buffer, or into the plan's node weights v_i. The FP32 remainders of
 // the nodes go to the host-node staging buffer (M x 3 doubles), which a
@@ -842,7 +893,10 @@ hamls_status hamls_sync(hamls_plan_t P, int timeout_ms) {
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
   unsigned f = P->st_host->flags;
+  const unsigned tc = P->st_host->tc_err;
   if (f) HAMLS_TRY(cudaMemsetAsync(&P->st->flags, 0, sizeof(unsigned), s));
+  if (tc) HAMLS_TRY(cudaMemsetAsync(&P->st->tc_err, 0, sizeof(unsigned), s));
+  if (tc && !f) return HAMLS_ERR_TIMEOUT;
   return hamls_status_from_flags(f);
 }
 
@@ -894,6 +948,8 @@ hamls_status hamls_destroy(hamls_plan_t P) {
       cudaEventDestroy(P->ev[i][1]);
     }
   if (P->arena.base) cudaFree(P->arena.base);
+  if (P->batch_mem) cudaFree(P->batch_mem);
+  tables_release(P->tables);
   if (P->shep_mem) cudaFree(P->shep_mem);
   if (P->op_mem) cudaFree(P->op_mem);
   if (P->st_host) cudaFreeHost(P->st_host);

@@ -39,7 +39,7 @@ enum { C_SUM_N = 0, C_MIN_N, C_MAX_N, C_REG, C_GUARD, C_REDO, C_DROP, C_GUARD_LI
 
 struct DevStatus {
   unsigned flags;
-  unsigned pad;
+  unsigned tc_err;          // tensor-core tiles that gave up waiting (batched step 3)
   unsigned long long cnt[16];
 };
 

@@ -125,19 +125,27 @@ __global__ void rec_kernel(int N, double* a_rec, double* b_rec) {
   }
 }
 
-// one thread per (m, folded column c): Pbar_l^m(t_c) for l = m..N
-__global__ void legendre_gen_kernel(int N, int hc, const double* __restrict__ t, const double* __restrict__ w,
-                                    const double* __restrict__ s, const double* __restrict__ a_rec,
-                                    const double* __restrict__ b_rec, double* __restrict__ A64,
-                                    float* __restrict__ A32) {
+// one thread per (m, folded column c): Pbar_l^m(t_c) for l = m..N. The FP64
+// matrix has rows in degree order and hc columns; the FP32 matrix has, within
+// each order m, the rows of even l - m first, then the odd ones (each parity
+// group contiguous, the operand of the batched tensor-core contraction), and
+// rows of hcp >= hc columns whose padding is zero.
+__global__ void legendre_gen_kernel(int N, int hc, int hcp, const double* __restrict__ t,
+                                    const double* __restrict__ w, const double* __restrict__ s,
+                                    const double* __restrict__ a_rec, const double* __restrict__ b_rec,
+                                    double* __restrict__ A64, float* __restrict__ A32) {
   const int m = blockIdx.y;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= hc) return;
+  const size_t row0 = (size_t)m * (N + 1) - (size_t)m * (m - 1) / 2;
+  if (c >= hc) {
+    if (A32 && c < hcp)
+      for (int l = m; l <= N; ++l) A32[(row0 + l32_row(N, m, l)) * hcp + c] = 0.f;
+    return;
+  }
   const double tc = t[c], sc = s[c];
   const double h = 2.0 * 3.14159265358979323846 / (2.0 * N + 2.0) * w[c];
   double pmm = 0.28209479177387814347;   // 1/sqrt(4 pi)
   for (int k = 1; k <= m; ++k) pmm *= -sqrt((2.0 * k + 1.0) / (2.0 * k)) * sc;
-  const size_t row0 = (size_t)m * (N + 1) - (size_t)m * (m - 1) / 2;
   double pm2 = 0.0, pm1 = 0.0;          // Pbar_{l-2}^m, Pbar_{l-1}^m
   for (int l = m; l <= N; ++l) {
     double p;
@@ -151,10 +159,9 @@ __global__ void legendre_gen_kernel(int N, int hc, const double* __restrict__ t,
     }
     pm2 = pm1;
     pm1 = p;
-    const size_t idx = (row0 + (l - m)) * hc + c;
     const double v = h * p;
-    if (A64) A64[idx] = v;
-    if (A32) A32[idx] = (float)v;
+    if (A64) A64[(row0 + (l - m)) * hc + c] = v;
+    if (A32) A32[(row0 + l32_row(N, m, l)) * hcp + c] = (float)v;
   }
 }
 
@@ -163,9 +170,9 @@ void build_grid_tables(GridTables& g, bool want32, bool want64, cudaStream_t s, 
   gl_kernel<<<(N + 2) / 2 / 128 + 1, 128, 0, s>>>(N, g.t, g.w, g.s, g.tf, g.sf);
   phi_kernel<<<(L + 255) / 256, 256, 0, s>>>(L, g.cphi, g.sphi, g.W64, want32 ? g.W32 : nullptr, g.cpf, g.spf);
   rec_kernel<<<N + 1, 256, 0, s>>>(N, g.a_rec, g.b_rec);
-  dim3 grid((g.hc + 63) / 64, N + 1);
-  legendre_gen_kernel<<<grid, 64, 0, s>>>(N, g.hc, g.t, g.w, g.s, g.a_rec, g.b_rec, want64 ? g.A64 : nullptr,
-                                          want32 ? g.A32 : nullptr);
+  dim3 grid((g.hcp + 63) / 64, N + 1);
+  legendre_gen_kernel<<<grid, 64, 0, s>>>(N, g.hc, g.hcp, g.t, g.w, g.s, g.a_rec, g.b_rec,
+                                          want64 ? g.A64 : nullptr, want32 ? g.A32 : nullptr);
   *launches += 4;
 }
 

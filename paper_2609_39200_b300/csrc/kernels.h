@@ -56,8 +56,51 @@ struct GridTables {
   float2* W32;
   float *tf, *sf, *cpf, *spf;   // FP32 copies of t, s, cphi, sphi (FP32 paths)
   int hc;                       // folded column count
+  int hcp;                      // row length of A32: hc rounded up to a multiple of 8 (16-byte rows)
 };
+
+// Row of degree l within order m's block of the FP32 quadrature matrix: the
+// even l - m first (l = m, m+2, ...), then the odd ones.
+__host__ __device__ __forceinline__ int l32_row(int N, int m, int l) {
+  const int i = l - m;
+  return (i & 1) ? (N - m) / 2 + 1 + (i >> 1) : (i >> 1);
+}
 void build_grid_tables(GridTables& g, bool want32, bool want64, cudaStream_t s, int64_t* launches);
+
+// ----------------------------------------------------------------- tcgemm.cu
+// One CTA tile of the tensor-core product D = A B^T: rows [a_y, a_y + 128)
+// of A (plus 128 blockIdx.y) at depth a_z, rows [b_y, b_y + nt) of B (nt a
+// multiple of 32, at most 256); e0..e3 belong to the epilogue.
+struct TcJob {
+  int a_y, a_z, b_y, nt;
+  int e0, e1, e2, e3;
+};
+// Tiles of the batched Legendre contraction at bandwidth N (out == nullptr:
+// count only): one per order m, parity and block of at most 256 degrees.
+int tc_legendre_jobs(int N, TcJob* out);
+// coeffs (B x ncoef complex, each set packed as hamls_fit) of the B value
+// sets whose folded spectra are G: 2(N+1) blocks (order m, parity) of 2B
+// rows (set b: real part row 2b, imaginary 2b+1) of hcp FP32 (hc used).
+cudaError_t tc_legendre(const GridTables& g, const float* G, int B, const TcJob* jobs, int njobs, double* coeffs,
+                        unsigned* err, cudaStream_t s, int64_t* launches);
+
+// ----------------------------------------------------------------- tables.cu
+struct SharedTables {
+  int device = 0, N = 0;
+  bool mixed = false;
+  GridTables g;
+  void* mem = nullptr;
+  cudaEvent_t ready = nullptr;
+  int refs = 0;
+  TcJob* jobs = nullptr;        // tensor-core Legendre tiles (mixed form)
+  int njobs = 0;
+};
+// the tables of (current device, N, form), built on s by the first user; later
+// users' streams wait for them. nullptr and *err on failure.
+SharedTables* tables_acquire(int N, bool mixed, cudaStream_t s, int64_t* launches, cudaError_t* err);
+void tables_release(SharedTables* t);
+size_t tables_bytes(int N, bool mixed);
+int tables_live();
 void fibonacci_points(double* x, double* y, double* z, int n, cudaStream_t s, int64_t* launches);
 
 // -------------------------------------------------------------------- knn.cu
@@ -160,6 +203,12 @@ struct QuadArgs {
 };
 // part: 1 = ring FFT, 2 = Legendre contraction, 3 = both
 void run_quadrature(const QuadArgs& a, bool mixed, cudaStream_t s, int64_t* launches, int part = 3);
+// step 3 of B value sets (mixed form): ring FFTs of fgrid (B x M_Q, set b at
+// b M_Q) into F (B x (N+1)^2 complex FP32), the folded spectra G, and the
+// tensor-core Legendre contraction into coeffs (B x ncoef complex)
+cudaError_t run_quadrature_batch(const GridTables& g, const int* radices, int nrad, const double* fgrid, int B,
+                                 float2* F, float* G, const TcJob* jobs, int njobs, double* coeffs, unsigned* err,
+                                 cudaStream_t s, int64_t* launches);
 
 // ---------------------------------------------------------------- voronoi.cu
 // Area of the spherical Voronoi cell of every point of g (FP32 area when

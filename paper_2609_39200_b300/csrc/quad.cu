@@ -15,6 +15,7 @@
 // matrix of grid.cu: for the northern columns c < hc the pair (c, N - c)
 // contributes A^m[l, c] (F_c + (-1)^{l+m} F_{N-c}). A single fit is a
 // matrix-vector product bound by HBM bandwidth on the matrix.
+#include <string.h>
 #include "common.cuh"
 #include "kernels.h"
 
@@ -38,6 +39,9 @@ __global__ void __launch_bounds__(256) ring_fft_kernel(const double* __restrict_
   cT* buf1 = buf0 + L;
   const int ra = 2 * blockIdx.x, rb = ra + 1;
   const bool hasb = rb <= N;
+  // value set blockIdx.y of a batch: grids M_Q apart, spectra (N+1)^2 apart
+  f += (size_t)blockIdx.y * (size_t)(N + 1) * L;
+  F += (size_t)blockIdx.y * (size_t)(N + 1) * (N + 1);
   for (int j = threadIdx.x; j < L; j += blockDim.x) {
     T x = (T)f[(size_t)ra * L + j];
     T y = hasb ? (T)f[(size_t)rb * L + j] : T(0);
@@ -98,8 +102,10 @@ __global__ void __launch_bounds__(256) ring_fft_kernel(const double* __restrict_
 // rows at once (coalesced, four loads in flight), reducing with shuffles.
 constexpr int LEG_ROWS = 32;
 
+// The matrix rows: degree order with hc columns (FP64), or the parity-grouped
+// FP32 layout (l32_row) with rows of ld columns.
 template <typename T>
-__global__ void __launch_bounds__(256) legendre_kernel(int N, int hc, const T* __restrict__ A,
+__global__ void __launch_bounds__(256) legendre_kernel(int N, int hc, int ld, bool grouped, const T* __restrict__ A,
                                                        const typename C2<T>::t* __restrict__ F,
                                                        double* __restrict__ coeffs) {
   using cT = typename C2<T>::t;
@@ -134,7 +140,8 @@ __global__ void __launch_bounds__(256) legendre_kernel(int N, int hc, const T* _
   for (int r = 0; r < 4; ++r) {
     sr[r] = si[r] = T(0);
     on[r] = lw + r <= N;
-    row[r] = A + (row0 + (on[r] ? lw + r - m : 0)) * hc;
+    const int l = on[r] ? lw + r : m;
+    row[r] = A + (row0 + (grouped ? l32_row(N, m, l) : l - m)) * ld;
   }
   for (int c = lane; c < hc; c += 32) {
     T av[4];
@@ -175,9 +182,72 @@ static void launch_quad(const QuadArgs& a, const typename C2<T>::t* W, const T* 
   }
   if (part & 2) {
     const dim3 grid(N + 1, (N + 1 + LEG_ROWS - 1) / LEG_ROWS);
-    legendre_kernel<T><<<grid, 256, smem_leg, s>>>(N, hc, A, reinterpret_cast<const cT*>(a.F), a.coeffs);
+    const bool grouped = sizeof(T) == 4;
+    legendre_kernel<T><<<grid, 256, smem_leg, s>>>(N, hc, grouped ? a.g->hcp : hc, grouped, A,
+                                                   reinterpret_cast<const cT*>(a.F), a.coeffs);
     ++*launches;
   }
+}
+
+// The folded spectra of a batch, the A operand of the tensor-core Legendre
+// contraction: for value set b, order m and column c < hc,
+//   E = F_c(m) + F_{N-c}(m),  O = F_c(m) - F_{N-c}(m)   (E = O = F_c(m) if c = N - c),
+// stored as G[(2m + p) * 2B + 2b + {0: re, 1: im}][c], p = 0 for E, 1 for O.
+// A 32 x 32 tile of (c, m) per block: reads along m, writes along c.
+__global__ void __launch_bounds__(256) fold_spectra_kernel(const float2* __restrict__ F, int N, int hc, int hcp,
+                                                           int B, float* __restrict__ G) {
+  __shared__ float2 E[32][33], O[32][33];
+  const int b = blockIdx.z, m0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const float2* Fb = F + (size_t)b * (N + 1) * (N + 1);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int c = c0 + r, m = m0 + tx;
+    float2 e = make_float2(0.f, 0.f), o = e;
+    if (c < hc && m <= N) {
+      const float2 a = Fb[(size_t)c * (N + 1) + m];
+      if (N - c != c) {
+        const float2 z = Fb[(size_t)(N - c) * (N + 1) + m];
+        e = make_float2(a.x + z.x, a.y + z.y);
+        o = make_float2(a.x - z.x, a.y - z.y);
+      } else {
+        e = a;
+        o = a;
+      }
+    }
+    E[tx][r] = e;
+    O[tx][r] = o;
+  }
+  __syncthreads();
+  const size_t rs = (size_t)hcp, ps = (size_t)2 * B * hcp;
+  for (int r = ty; r < 32; r += 8) {
+    const int m = m0 + r, c = c0 + tx;
+    if (m > N || c >= hc) continue;
+    float* ge = G + (size_t)(2 * m) * ps + (size_t)(2 * b) * rs + c;
+    float* go = ge + ps;
+    ge[0] = E[r][tx].x;
+    ge[rs] = E[r][tx].y;
+    go[0] = O[r][tx].x;
+    go[rs] = O[r][tx].y;
+  }
+}
+
+cudaError_t run_quadrature_batch(const GridTables& g, const int* radices, int nrad, const double* fgrid, int B,
+                                 float2* F, float* G, const TcJob* jobs, int njobs, double* coeffs, unsigned* err,
+                                 cudaStream_t s, int64_t* launches) {
+  const int N = g.N, L = 2 * N + 2;
+  QuadArgs qa;
+  memset(&qa, 0, sizeof(qa));
+  qa.g = &g;
+  for (int i = 0; i < nrad; ++i) qa.radices[i] = radices[i];
+  qa.nrad = nrad;
+  static unsigned done_fft = 0;
+  set_smem_attr_once((const void*)ring_fft_kernel<float>, 200 * 1024, &done_fft);
+  ring_fft_kernel<float><<<dim3((N + 2) / 2, B), 256, 2 * (size_t)L * sizeof(float2), s>>>(fgrid, N, qa, g.W32, F);
+  fold_spectra_kernel<<<dim3((N + 1 + 31) / 32, (g.hc + 31) / 32, B), 256, 0, s>>>(F, N, g.hc, g.hcp, B, G);
+  *launches += 2;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return tc_legendre(g, G, B, jobs, njobs, coeffs, err, s, launches);
 }
 
 void run_quadrature(const QuadArgs& a, bool mixed, cudaStream_t s, int64_t* launches, int part) {
