@@ -58,6 +58,11 @@ def parse():
     ap.add_argument("--cache", default=None, help="directory to keep/reuse the generated workload (profiling runs)")
     ap.add_argument("--fp64-pivot", type=float, default=None, help="mixed form: squared FP32 pivot below which a "
                     "local solve is redone in FP64 (library default if omitted)")
+    ap.add_argument("--batch-sets", type=int, default=64, help="value sets of the many-sets leg (0: skip)")
+    ap.add_argument("--batch-fits", type=int, default=256, help="fits of the batched leg (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests per arrival rate of the serving leg "
+                    "(0: skip)")
+    ap.add_argument("--serve-rates", default="40,80,160", help="arrival rates (requests/s) of the serving leg")
     return ap.parse_args()
 
 
@@ -273,6 +278,164 @@ def load_workload(cache, rank, torch, dev):
     return w
 
 
+def many_sets_leg(h, plan, w, y, flush, stream, B, steps, warmup, peaks, truth_err):
+    """Refits of B value sets at the plan's (prepared) nodes with
+    hamls_refit_batch, and step 3 of B grids with hamls_quadrature_batch; the
+    tensor-core contraction's own roofline from its stage events."""
+    import torch
+
+    dev = y.device
+    N = w.N
+    ncoef = (N + 1) * (N + 2) // 2
+    MQ = (N + 1) * (2 * N + 2)
+    hc = N // 2 + 1
+    hcp = (hc + 7) // 8 * 8
+    scales = torch.linspace(1.0, 2.0, B, dtype=torch.float64, device=dev)
+    Y = (scales[:, None] * y[None, :]).contiguous()         # set 0: the workload's values
+    out = torch.empty((B, ncoef, 2), dtype=torch.float64, device=dev)
+
+    def timed(fn):
+        plan.set_timing(True)
+        ts, st = [], []
+        for i in range(warmup + steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if i >= warmup:
+                ts.append(e0.elapsed_time(e1))
+                st.append(plan.stage_times())
+        plan.set_timing(False)
+        plan.sync(600000)
+        return np.array(ts), {k: float(np.mean([d[k] for d in st])) for k in st[0]}
+
+    ts, st = timed(lambda: plan.refit_batch(Y, out=out))
+    c0 = h.to_complex(out[0])
+    lin = float(np.linalg.norm(h.to_complex(out[B - 1]) - 2.0 * c0) / np.linalg.norm(2.0 * c0))
+    refit = {"sets": B, "value": B * len(ts) / (float(ts.sum()) / 1000.0), "unit": "fits/s",
+             "ms_per_call": float(ts.mean()), "l2_error_set0": truth_err(c0),
+             "linearity_rel_err": lin, "stage_ms": {k: round(v, 4) for k, v in st.items() if v >= 0}}
+    # step 3 alone for B grids (the last refit's grid values, scaled)
+    g = plan.debug_grid()["f"]
+    F = (scales[:, None] * g[None, :]).contiguous()
+    ts, st = timed(lambda: plan.quadrature_batch(F, out=out))
+    t_tc = st["legendre"] / 1000.0
+    # executed tensor work: 3 products per term, K padded to 32, value-set parts
+    # padded to 128 rows, degrees of each (order, parity) block padded to 32
+    rows_pad = 0
+    for m in range(N + 1):
+        for cnt in ((N - m) // 2 + 1, (N - m + 1) // 2):
+            rows_pad += -(-cnt // 32) * 32 if cnt else 0
+    kp = -(-hc // 32) * 32
+    mt = -(-2 * B // 128) * 128
+    flops_exec = 3 * 2 * rows_pad * kp * mt
+    flops_alg = 2 * ncoef * hc * 2 * B
+    # DRAM bytes as stored: matrix hi + lo, folded spectra hi + lo, coefficients out
+    bytes_alg = 2 * ncoef * hcp * 4 + 2 * (2 * (N + 1)) * (2 * B) * hcp * 4 + B * ncoef * 16
+    tf32_peak = float(peaks.get("bf16_tflops", 1800.0)) * 0.5
+    quad = {"sets": B, "value": B * len(ts) / (float(ts.sum()) / 1000.0), "unit": "grids/s",
+            "ms_per_call": float(ts.mean()), "spectra_ms": st["fft"], "tensor_ms": st["legendre"],
+            "roofline": {"bound": "hbm", "kernel": "tc_gemm_kernel<EpiLegendre> (tcgen05 kind::tf32, 3xTF32)",
+                         "achieved": bytes_alg / t_tc / 1e9, "peak": float(peaks.get("hbm_gbs", 6400.0)),
+                         "unit": "GB/s", "frac": bytes_alg / t_tc / 1e9 / float(peaks.get("hbm_gbs", 6400.0)),
+                         "traffic": None, "algorithmic_bytes_per_launch": int(bytes_alg)},
+            "tensor": {"achieved_tflops_executed": flops_exec / t_tc / 1e12,
+                       "achieved_tflops_fp32_equivalent": flops_alg / t_tc / 1e12,
+                       "peak_tf32_tflops": tf32_peak, "peak_source": "measured bf16 x 0.5 (nominal tf32/bf16)",
+                       "frac_executed": flops_exec / t_tc / 1e12 / tf32_peak}}
+    del Y, F
+    return {"refit_batch": refit, "quadrature_batch": quad}
+
+
+def batched_leg(h, dev, n_fits, precision="mixed"):
+    """Config 4: n_fits independent fits (N over {32, 64, 128, 256}, M
+    log-uniform in [1e4, 1e6], K over {2, 3}, 0-3 holes) replanned and fitted
+    from reserved plans, the whole batch captured in one CUDA graph and
+    replayed; the stream concurrency is chosen by the slot autotuner. Node sets
+    are seeded; values come from a degree-32 field (their content does not
+    change the work)."""
+    import torch
+
+    from hamls_synth import batch_specs, fit_workload
+    from paper_2609_39200_b300.batch import PlanPool, SlotTuner, run_batch
+
+    specs = batch_specs(n_fits)
+    t0 = time.perf_counter()
+    inputs = {}
+    for s in specs:
+        wl = fit_workload(s, xp=torch, device=dev, L_field=32)
+        inputs[s.index] = (torch.tensor(wl.nodes, device=dev), torch.tensor(wl.values, device=dev))
+    gen_s = time.perf_counter() - t0
+
+    def load(s):
+        return inputs[s.index]
+
+    pool = PlanPool(device=dev, min_capacity=1 << 14)
+    tuner = SlotTuner((2, 4, 8))
+    slots = tuner.choose(specs, load, pool, precision=precision, device=dev)
+    reps = 3
+    r = run_batch(specs, load, pool, n_slots=slots, precision=precision, device=dev, graph=True, replays=reps)
+    bad = [{"index": s.index, "N": s.N, "K": s.K, "M": s.M, "holes": len(s.holes_deg), "status": int(x)}
+           for s, x in zip(specs, r.status) if x]
+    res = {"fits": n_fits, "value": n_fits * reps / r.seconds, "unit": "fits/s", "ms_per_batch": 1000 * r.seconds / reps,
+           "slots": slots, "autotune_s_per_batch": {str(k): round(v, 4) for k, v in
+                                                     tuner.trials[tuner.shape(specs, pool.min_capacity)].items()},
+           "graph": r.graph, "plans": pool.created, "plan_bytes": pool.used_bytes, "failed_fits": len(bad),
+           "failures": bad[:16],
+           "grid_nodes": int(sum((s.N + 1) * (2 * s.N + 2) for s in specs)), "input_generation_s": round(gen_s, 1),
+           "note": "one CUDA graph replay runs every replan, fit and status copy of the batch"}
+    res["grid_nodes_per_s"] = res["grid_nodes"] * res["value"] / n_fits
+    pool.close()
+    del inputs
+    return res
+
+
+def serving_leg(h, dev, n_req, rates, precision="mixed"):
+    """Config 5: Poisson arrivals of fit requests (N over {64..1024} with
+    probabilities {.3, .3, .2, .15, .05}, M log-uniform in [5e4, 1.6e7], K = 3,
+    three holes) served by continuous batching over 4 slots, plans kept on the
+    device and admitted by their memory footprint. A request's nodes are the
+    first M of one seeded 16M-node track/hole set (the same distribution), its
+    values a degree-32 field. The trace is served once to create the plans,
+    then at each rate; latency runs from arrival to the end of the fit."""
+    import torch
+
+    from hamls_synth import random_field_coeffs, serving_trace, synth_field, track_hole_nodes
+    from paper_2609_39200_b300.batch import PlanPool, serve
+
+    t0 = time.perf_counter()
+    Mmax = 16_000_000
+    xn = track_hole_nodes(0x48414D4C53 ^ (5 << 32), Mmax)[0]
+    X = torch.tensor(xn, device=dev)
+    Yv = synth_field(random_field_coeffs(55, 32), X, torch).contiguous()
+    gen_s = time.perf_counter() - t0
+
+    def load(r):
+        return X[:r.M], Yv[:r.M]
+
+    free, _ = torch.cuda.mem_get_info(dev)
+    pool = PlanPool(device=dev, budget_bytes=int(0.6 * free), min_capacity=1 << 16)
+    out = {"requests_per_rate": n_req, "slots": 4, "input_generation_s": round(gen_s, 1), "rates": {}}
+    warm = serving_trace(1e6, n_req)
+    serve(warm, load, pool, n_slots=4, precision=precision, device=dev, keep_outputs=False)
+    for lam in rates:
+        tr = serving_trace(lam, n_req)
+        r = serve(tr, load, pool, n_slots=4, precision=precision, device=dev, keep_outputs=False)
+        lat = r.latency_s * 1000.0
+        out["rates"][str(lam)] = {"fits_per_s": n_req / r.makespan_s, "p50_ms": float(np.percentile(lat, 50)),
+                                  "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+                                  "queue_p99_ms": float(np.percentile(r.queue_s * 1000.0, 99)),
+                                  "failed": int(sum(1 for x in r.status if x))}
+    out["plans"] = pool.created
+    out["evicted"] = pool.evicted
+    out["plan_bytes"] = pool.used_bytes
+    pool.close()
+    del X, Yv
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -386,6 +549,31 @@ def run_ours(args):
                               "algorithmic_bytes_per_launch": int(op_bytes), "ms_per_launch": a_ms},
                  "note": "new values at the plan's nodes: the stored operator, then ring FFT and Legendre"}
 
+    # ---- many value sets at the plan's nodes (tensor-core step 3); the
+    # batched form (config 4) and the serving trace (config 5)
+    def truth_err_fn(c):
+        import oracle as O   # packing helpers only
+        N = w.N
+        Lt = w.truth.shape[0] - 1
+        t = np.zeros((max(N, Lt) + 1,) * 2, complex)
+        t[:Lt + 1, :Lt + 1] = np.tril(w.truth)
+        t[:N + 1, :N + 1] -= O.unpack_coeffs(c, N)
+        d2 = np.sum(np.abs(t[:, 0]) ** 2) + 2 * np.sum(np.abs(t[:, 1:]) ** 2)
+        return float(math.sqrt(d2 / coeff_norm2(w.truth)))
+
+    peaks0 = {}
+    try:
+        peaks0 = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    many = batched = serving = None
+    if not args.quick and refit is not None and args.batch_sets > 0:
+        try:
+            many = many_sets_leg(h, plan, w, y, flush, stream, args.batch_sets, max(3, args.steps // 10), 2, peaks0,
+                                 truth_err_fn)
+        except Exception as e:                  # reported, never fatal to the headline line
+            many = {"error": f"{type(e).__name__}: {e}"[:300]}
+
     # ---- Voronoi areas of the nodes (the weights v_i of Sec. 2.2, computed once
     # per node set): CUDA events around hamls_voronoi_areas, L2 flushed between calls
     def voronoi_leg(pl, reps):
@@ -457,6 +645,17 @@ def run_ours(args):
                "timing": "host wall clock over all steps, both streams synchronised at the end",
                "pipelining": "two plans on two streams take alternate steps"}
     plan.close()
+
+    if not args.quick and args.batch_fits > 0 and world == 1:
+        try:
+            batched = batched_leg(h, dev, args.batch_fits)
+        except Exception as e:
+            batched = {"error": f"{type(e).__name__}: {e}"[:300]}
+    if not args.quick and args.serve_requests > 0 and world == 1:
+        try:
+            serving = serving_leg(h, dev, args.serve_requests, [float(r) for r in args.serve_rates.split(",")])
+        except Exception as e:
+            serving = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     # ---- FP64 form (the comparison)
     fp64 = None
@@ -552,7 +751,8 @@ def run_ours(args):
                 "grid_nodes_per_s": value * MQ,
                 "stage_ms": {k: round(v, 4) for k, v in stages.items()},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk.summary(), "fp64_form": fp64, "refit": refit, "voronoi": voronoi, "l2_error": l2,
+                "clocks": clk.summary(), "fp64_form": fp64, "refit": refit, "many_sets": many,
+                "batched": batched, "serving": serving, "voronoi": voronoi, "l2_error": l2,
                 "mls_stats": {k: stats[k] for k in ("sum_n", "min_n", "max_n", "n_regularized", "n_guarded",
                                                     "n_fp64_redo", "n_dropped")},
                 "knn_stats": {k: stats[k] for k in stats if k.startswith("knn_") or k == "aux_points"}}

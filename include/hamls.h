@@ -182,7 +182,7 @@ hamls_status hamls_fit(hamls_plan_t plan, const double* values, double* coeffs, 
  *   coeffs  B x (N+1)(N+2)/2 complex (device), each set packed as hamls_fit
  *   B       1 <= B <= 65535
  * The first call with a given B allocates the workspace (spectra and folded
- * spectra, about B (N+1)^2 16 B; owned by the plan, reused by later calls of
+ * spectra, about B (N+1)^2 24 B; owned by the plan, reused by later calls of
  * B or fewer sets) and, when it grows, waits for the plan's stream. A tile
  * whose copies or products did not arrive within about 2 s is reported by
  * hamls_sync as HAMLS_ERR_TIMEOUT.
@@ -217,6 +217,20 @@ hamls_status hamls_quadrature_batch(hamls_plan_t plan, const double* fgrid, doub
  */
 hamls_status hamls_refit_prepare(hamls_plan_t plan, cudaStream_t stream);
 hamls_status hamls_refit(hamls_plan_t plan, const double* values, double* coeffs, cudaStream_t stream);
+
+/*
+ * hamls_refit_batch - hamls_refit for B value sets at the prepared nodes at
+ * once (a time series on fixed stations): the operator is read once for all
+ * sets, and step 3 is hamls_quadrature_batch's (tensor cores, MIXED plans).
+ *   values  B x M doubles (device): set b at b M, in the node order of the plan
+ *   coeffs  B x (N+1)(N+2)/2 complex (device), each set packed as hamls_fit
+ * MIXED plans take up to 256 sets per pass (more are done in passes) and
+ * allocate their workspace on the first call with a larger pass (about
+ * (8 M + 12 M_Q) bytes per set, plus hamls_quadrature_batch's; owned by the
+ * plan), waiting for the stream when it grows. FP64 plans refit set by set.
+ * HAMLS_ERR_INVALID_ARG without a prepared operator or for host pointers.
+ */
+hamls_status hamls_refit_batch(hamls_plan_t plan, const double* values, double* coeffs, int B, cudaStream_t stream);
 
 /*
  * hamls_voronoi_areas - the area of the spherical Voronoi cell of every node

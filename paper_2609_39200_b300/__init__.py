@@ -66,6 +66,7 @@ _SIGS = {
     "hamls_quadrature_batch": (_I, [_P, _P, _P, _I, _P]),
     "hamls_refit_prepare": (_I, [_P, _P]),
     "hamls_refit": (_I, [_P, _P, _P, _P]),
+    "hamls_refit_batch": (_I, [_P, _P, _P, _I, _P]),
     "hamls_voronoi_areas": (_I, [_P, _P, _P]),
     "hamls_voronoi_weights": (_I, [_P, _P]),
     "hamls_sync": (_I, [_P, _I]),
@@ -209,6 +210,16 @@ class Plan:
             out = torch.empty((n_coeffs(self.N), 2), dtype=torch.float64, device=dev)
         self._keep_refit = (values, out)
         _check(lib().hamls_refit(self.h, _ptr(values), _ptr(out), _stream(stream)), "hamls_refit")
+        return out
+
+    def refit_batch(self, values, out=None, stream=None):
+        """Coefficients (B, ncoef, 2) for B value sets (B x M float64 device
+        tensor) at the prepared nodes."""
+        B = int(values.shape[0])
+        if out is None:
+            out = torch.empty((B, n_coeffs(self.N), 2), dtype=torch.float64, device=values.device)
+        self._keep_rb = (values, out)
+        _check(lib().hamls_refit_batch(self.h, _ptr(values), _ptr(out), B, _stream(stream)), "hamls_refit_batch")
         return out
 
     def voronoi_areas(self, out=None, stream=None):

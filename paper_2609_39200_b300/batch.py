@@ -404,3 +404,33 @@ def serve(trace: Sequence, load: Callable, pool: PlanPool, n_slots: int = 4, pre
         else:
             lat[i] = done_host[i] - trace[i].arrival_s
     return ServeResult(lat, queue, outs, stat, slot_of, makespan, issued)
+
+
+class SlotTuner:
+    """Autotuner of the batched form's launch configuration: the number of
+    concurrent streams (slots) a batch is spread over. For each batch shape
+    (the multiset of (N, K) and the capacity classes) it times one graph
+    replay per candidate the first time the shape is seen and keeps the
+    fastest; later batches of the same shape reuse the choice."""
+
+    def __init__(self, candidates=(2, 4, 8)):
+        self.candidates = tuple(candidates)
+        self.cache: Dict[tuple, int] = {}
+        self.trials: Dict[tuple, Dict[int, float]] = {}
+
+    @staticmethod
+    def shape(fits, min_capacity=1 << 16) -> tuple:
+        return tuple(sorted((s.N, s.K, capacity_class(s.M, min_capacity)) for s in fits))
+
+    def choose(self, fits, load, pool: PlanPool, precision="mixed", device=None) -> int:
+        key = self.shape(fits, pool.min_capacity)
+        if key in self.cache:
+            return self.cache[key]
+        times = {}
+        for n in self.candidates:
+            r = run_batch(fits, load, pool, n_slots=n, precision=precision, device=device, graph=device is not None)
+            times[n] = r.seconds
+        best = min(times, key=times.get)
+        self.cache[key] = best
+        self.trials[key] = times
+        return best

@@ -88,8 +88,14 @@ struct hamls_plan_s {
   // to batch_cap value sets, allocated on first use and grown as needed
   void* batch_mem = nullptr;
   int batch_cap = 0;
+  // refits of many value sets (hamls_refit_batch): transposed values, grid
+  // values of each set (FP32, then FP64 for step 3), up to rb_cap sets
+  void* rb_mem = nullptr;
+  int rb_cap = 0;
+  float *rb_yo = nullptr, *rb_yT = nullptr, *rb_fT = nullptr;
+  double* rb_f = nullptr;
   float2* batch_F = nullptr;
-  float* batch_G = nullptr;
+  float *batch_G = nullptr, *batch_Glo = nullptr;
   unsigned* batch_err = nullptr;
   // scattered nodes: the cell structure (B bands, P cells per band) follows
   // the current node count; Bcap is the largest one the arena holds
@@ -123,6 +129,7 @@ struct hamls_plan_s {
   void* op_val = nullptr;
   double* op_gamma = nullptr;
   float* op_yf = nullptr;          // MIXED: the values in FP32 for a refit
+  uint32_t* op_long = nullptr;     // count, then the rows of more than 256 entries
   unsigned long long op_nnz = 0;
   bool op_valid = false;
   // grid nodes
@@ -756,7 +763,8 @@ hamls_status hamls_refit_prepare(hamls_plan_t P, cudaStream_t s) {
   const size_t nrow = (size_t)P->MQ + 1, ny = (size_t)value_moment_count(P->K);
   const size_t b_rows = up(nrow * 4), b_col = up(total * 4 + 4), b_val = up(total * vsz + vsz);
   const size_t b_gamma = up((size_t)P->MQ * ny * sizeof(double));
-  const size_t need = b_rows + b_col + b_val + b_gamma + up((size_t)P->Mcap * sizeof(float));
+  const size_t b_long = up(((size_t)P->MQ + 1) * 4);
+  const size_t need = b_rows + b_col + b_val + b_gamma + up((size_t)P->Mcap * sizeof(float)) + b_long;
   if (P->op_bytes < need) {
     if (P->op_mem) cudaFree(P->op_mem);
     P->op_mem = nullptr;
@@ -770,10 +778,12 @@ hamls_status hamls_refit_prepare(hamls_plan_t P, cudaStream_t s) {
   P->op_val = base + b_rows + b_col;
   P->op_gamma = reinterpret_cast<double*>(base + b_rows + b_col + b_val);
   P->op_yf = reinterpret_cast<float*>(base + b_rows + b_col + b_val + b_gamma);
+  P->op_long = reinterpret_cast<uint32_t*>(base + b_rows + b_col + b_val + b_gamma + up((size_t)P->Mcap * sizeof(float)));
   HAMLS_TRY(cudaMemcpyAsync(P->op_rows, P->okeys_alt, (size_t)P->MQ * 4, cudaMemcpyDeviceToDevice, s));
   HAMLS_TRY(cudaMemsetAsync(P->op_rows + P->MQ, 0, 4, s));
   exclusive_scan_u32(P->op_rows, P->MQ + 1, P->counts, s, &P->launches);
   run_refit_operator(a, P->mixed, 1, P->op_gamma, P->op_rows, P->op_col, P->op_val, nullptr, s, &P->launches);
+  list_long_rows(P->MQ, P->op_rows, P->op_long + 1, P->op_long, s, &P->launches);
   P->op_nnz = total;
   P->op_valid = true;
   P->last = s;
@@ -789,59 +799,124 @@ hamls_status hamls_refit(hamls_plan_t P, const double* values, double* coeffs, c
     dv = P->in_vals;
   }
   stage_begin(P, 5, s);
-  run_refit_apply(P->MQ, P->mixed, P->op_rows, P->op_col, P->op_val, dv, (int)P->M, P->op_yf, P->fgrid, P->st, s,
+  run_refit_apply(P->MQ, P->mixed, P->op_rows, P->op_col, P->op_val, dv, P->perm, (int)P->M, P->op_yf, P->sy,
+                  P->fgrid, P->st, s,
                   &P->launches);
   stage_end(P, 5, s);
   return run_step3(P, coeffs, s);
 }
 
-hamls_status hamls_quadrature_batch(hamls_plan_t P, const double* fgrid, double* coeffs, int B, cudaStream_t s) {
-  if (!P || !fgrid || !coeffs || B < 1 || B > 65535) return HAMLS_ERR_INVALID_ARG;
-  if (!is_device_ptr(fgrid) || !is_device_ptr(coeffs)) return HAMLS_ERR_INVALID_ARG;
+// step 3 of B grids (device), MIXED plans: workspace grown as needed
+static hamls_status quad_batch_mixed(hamls_plan_s* P, const double* fgrid, double* coeffs, int B, cudaStream_t s) {
   const int N = P->N;
-  const size_t ncoef = (size_t)(N + 1) * (N + 2) / 2;
-  if (!P->mixed) {
-    // the FP64 form: its own contraction per value set (the tensor cores
-    // carry FP32 accuracy only)
-    for (int b = 0; b < B; ++b) {
-      QuadArgs q;
-      memset(&q, 0, sizeof(q));
-      q.g = &P->g;
-      q.fgrid = fgrid + (size_t)b * P->MQ;
-      q.F = P->F;
-      q.coeffs = coeffs + (size_t)b * ncoef * 2;
-      for (int i = 0; i < P->nrad; ++i) q.radices[i] = P->radices[i];
-      q.nrad = P->nrad;
-      run_quadrature(q, false, s, &P->launches);
-    }
-    P->last = s;
-    return cuda_status(cudaGetLastError());
-  }
   if (B > P->batch_cap) {
     // workspace for B sets: spectra B (N+1)^2 complex FP32, folded spectra
     // 2 (N+1) x 2B x hcp FP32, an error word
     if (P->batch_mem) {
       HAMLS_TRY(cudaStreamSynchronize(P->last));
+      HAMLS_TRY(cudaStreamSynchronize(s));
       cudaFree(P->batch_mem);
       P->batch_mem = nullptr;
       P->batch_cap = 0;
     }
     const size_t bF = ((size_t)B * (N + 1) * (N + 1) * sizeof(float2) + 255) & ~size_t(255);
     const size_t bG = ((size_t)2 * (N + 1) * 2 * B * P->g.hcp * sizeof(float) + 255) & ~size_t(255);
-    HAMLS_TRY(cudaMalloc(&P->batch_mem, bF + bG + 256));
+    HAMLS_TRY(cudaMalloc(&P->batch_mem, bF + 2 * bG + 256));
     P->batch_F = reinterpret_cast<float2*>(P->batch_mem);
     P->batch_G = reinterpret_cast<float*>(reinterpret_cast<char*>(P->batch_mem) + bF);
-    P->batch_err = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(P->batch_mem) + bF + bG);
+    P->batch_Glo = reinterpret_cast<float*>(reinterpret_cast<char*>(P->batch_mem) + bF + bG);
+    P->batch_err = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(P->batch_mem) + bF + 2 * bG);
     P->batch_cap = B;
   }
   HAMLS_TRY(cudaMemsetAsync(P->batch_err, 0, sizeof(unsigned), s));
   stage_begin(P, 6, s);
-  cudaError_t e = run_quadrature_batch(P->g, P->radices, P->nrad, fgrid, B, P->batch_F, P->batch_G,
-                                       P->tables->jobs, P->tables->njobs, coeffs, P->batch_err, s, &P->launches);
+  cudaError_t e = run_spectra_batch(P->g, P->radices, P->nrad, fgrid, B, P->batch_F, P->batch_G, P->batch_Glo, s,
+                                    &P->launches);
   stage_end(P, 6, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  stage_begin(P, 7, s);
+  e = tc_legendre(P->g, P->batch_G, P->batch_Glo, B, P->tables->jobs, P->tables->njobs, coeffs, P->batch_err, s,
+                  &P->launches);
+  stage_end(P, 7, s);
   if (e != cudaSuccess) return cuda_status(e);
   // a tile that gave up waiting is reported by hamls_sync
   HAMLS_TRY(cudaMemcpyAsync(&P->st->tc_err, P->batch_err, sizeof(unsigned), cudaMemcpyDeviceToDevice, s));
+  P->last = s;
+  return cuda_status(cudaGetLastError());
+}
+
+// step 3 of one grid (device) into coeffs (device), FP64 or FP32 contraction
+static void quad_one(hamls_plan_s* P, const double* fgrid, double* coeffs, cudaStream_t s) {
+  QuadArgs q;
+  memset(&q, 0, sizeof(q));
+  q.g = &P->g;
+  q.fgrid = fgrid;
+  q.F = P->F;
+  q.coeffs = coeffs;
+  for (int i = 0; i < P->nrad; ++i) q.radices[i] = P->radices[i];
+  q.nrad = P->nrad;
+  run_quadrature(q, P->mixed, s, &P->launches);
+}
+
+hamls_status hamls_quadrature_batch(hamls_plan_t P, const double* fgrid, double* coeffs, int B, cudaStream_t s) {
+  if (!P || !fgrid || !coeffs || B < 1 || B > 65535) return HAMLS_ERR_INVALID_ARG;
+  if (!is_device_ptr(fgrid) || !is_device_ptr(coeffs)) return HAMLS_ERR_INVALID_ARG;
+  const size_t ncoef = (size_t)(P->N + 1) * (P->N + 2) / 2;
+  if (!P->mixed) {
+    // the FP64 form: its own contraction per value set (the tensor cores
+    // carry FP32 accuracy only)
+    for (int b = 0; b < B; ++b) quad_one(P, fgrid + (size_t)b * P->MQ, coeffs + (size_t)b * ncoef * 2, s);
+    P->last = s;
+    return cuda_status(cudaGetLastError());
+  }
+  return quad_batch_mixed(P, fgrid, coeffs, B, s);
+}
+
+hamls_status hamls_refit_batch(hamls_plan_t P, const double* values, double* coeffs, int B, cudaStream_t s) {
+  if (!P || !values || !coeffs || B < 1) return HAMLS_ERR_INVALID_ARG;
+  if (!P->op_valid) return HAMLS_ERR_INVALID_ARG;
+  if (!is_device_ptr(values) || !is_device_ptr(coeffs)) return HAMLS_ERR_INVALID_ARG;
+  const size_t ncoef = (size_t)(P->N + 1) * (P->N + 2) / 2;
+  const int64_t M = P->M;
+  if (!P->mixed) {
+    for (int b = 0; b < B; ++b) {
+      run_refit_apply(P->MQ, false, P->op_rows, P->op_col, P->op_val, values + (size_t)b * M, P->perm, (int)M,
+                      P->op_yf, P->sy, P->fgrid, P->st, s, &P->launches);
+      quad_one(P, P->fgrid, coeffs + (size_t)b * ncoef * 2, s);
+    }
+    P->last = s;
+    return cuda_status(cudaGetLastError());
+  }
+  const int chunk = B < 256 ? B : 256;
+  if (chunk > P->rb_cap) {
+    if (P->rb_mem) {
+      HAMLS_TRY(cudaStreamSynchronize(P->last));
+      HAMLS_TRY(cudaStreamSynchronize(s));
+      cudaFree(P->rb_mem);
+      P->rb_mem = nullptr;
+      P->rb_cap = 0;
+    }
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t by = up((size_t)P->Mcap * chunk * 4), bfT = up((size_t)P->MQ * chunk * 4);
+    const size_t bf = up((size_t)P->MQ * chunk * 8);
+    HAMLS_TRY(cudaMalloc(&P->rb_mem, 2 * by + bfT + bf));
+    char* rb = reinterpret_cast<char*>(P->rb_mem);
+    P->rb_yo = reinterpret_cast<float*>(rb);
+    P->rb_yT = reinterpret_cast<float*>(rb + by);
+    P->rb_fT = reinterpret_cast<float*>(rb + 2 * by);
+    P->rb_f = reinterpret_cast<double*>(rb + 2 * by + bfT);
+    P->rb_cap = chunk;
+  }
+  for (int b0 = 0; b0 < B; b0 += chunk) {
+    const int nb = B - b0 < chunk ? B - b0 : chunk;
+    stage_begin(P, 5, s);
+    run_refit_apply_batch(P->MQ, P->op_rows, P->op_col, reinterpret_cast<const float*>(P->op_val),
+                          values + (size_t)b0 * M, P->perm, (int)M, nb, P->rb_yo, P->rb_yT, P->rb_fT, P->rb_f,
+                          P->op_long + 1, P->op_long, P->st, s, &P->launches);
+    stage_end(P, 5, s);
+    const hamls_status r = quad_batch_mixed(P, P->rb_f, coeffs + (size_t)b0 * ncoef * 2, nb, s);
+    if (r != HAMLS_OK) return r;
+  }
   P->last = s;
   return cuda_status(cudaGetLastError());
 }
@@ -949,6 +1024,7 @@ hamls_status hamls_destroy(hamls_plan_t P) {
     }
   if (P->arena.base) cudaFree(P->arena.base);
   if (P->batch_mem) cudaFree(P->batch_mem);
+  if (P->rb_mem) cudaFree(P->rb_mem);
   tables_release(P->tables);
   if (P->shep_mem) cudaFree(P->shep_mem);
   if (P->op_mem) cudaFree(P->op_mem);

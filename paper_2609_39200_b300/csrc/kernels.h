@@ -52,6 +52,7 @@ struct GridTables {
   double *a_rec, *b_rec;        // packed (N+1)(N+2)/2 recurrence coefficients
   double* A64;                  // folded Legendre quadrature matrix, ncoef x hc
   float* A32;
+  float *A32hi, *A32lo;         // A32 split for 3xTF32 products: hi exact in TF32, lo = A32 - hi
   double2* W64;                 // FFT twiddles exp(-2 pi i j / L), L = 2N+2
   float2* W32;
   float *tf, *sf, *cpf, *spf;   // FP32 copies of t, s, cphi, sphi (FP32 paths)
@@ -79,10 +80,12 @@ struct TcJob {
 // count only): one per order m, parity and block of at most 256 degrees.
 int tc_legendre_jobs(int N, TcJob* out);
 // coeffs (B x ncoef complex, each set packed as hamls_fit) of the B value
-// sets whose folded spectra are G: 2(N+1) blocks (order m, parity) of 2B
-// rows (set b: real part row 2b, imaginary 2b+1) of hcp FP32 (hc used).
-cudaError_t tc_legendre(const GridTables& g, const float* G, int B, const TcJob* jobs, int njobs, double* coeffs,
-                        unsigned* err, cudaStream_t s, int64_t* launches);
+// sets whose folded spectra are Ghi + Glo: 2(N+1) blocks (order m, parity)
+// of 2B rows (set b: real part row 2b, imaginary 2b+1) of hcp FP32 (hc used)
+cudaError_t tc_legendre(const GridTables& g, const float* Ghi, const float* Glo, int B, const TcJob* jobs, int njobs,
+                        double* coeffs, unsigned* err, cudaStream_t s, int64_t* launches);
+// x_hi (the low 13 mantissa bits cleared: exact in TF32) and x_lo = x - x_hi
+void split_tf32(const float* x, size_t n, float* hi, float* lo, cudaStream_t s, int64_t* launches);
 
 // ----------------------------------------------------------------- tables.cu
 struct SharedTables {
@@ -184,11 +187,23 @@ void run_mls(const MlsArgs& a, bool mixed, cudaStream_t s, int64_t* launches, in
 // *total); part 1 = gamma per grid node, then the operator (rows = CSR start)
 void run_refit_operator(const MlsArgs& a, bool mixed, int part, double* gamma, uint32_t* rows, uint32_t* col,
                         void* val, unsigned long long* total, cudaStream_t s, int64_t* launches);
-// f = A y over the plan's grid; val is float (MIXED, with y converted into
-// yf, M floats) or double (FP64)
+// f = A y over the plan's grid: y (node order) is gathered into the cell
+// order of the operator's columns (perm: cell position -> node), as FP32 in
+// yf (MIXED, float entries) or FP64 in ys (FP64, double entries)
 void run_refit_apply(int MQ, bool mixed, const uint32_t* rows, const uint32_t* col, const void* val,
-                     const double* y, int M, float* yf, double* f, DevStatus* st, cudaStream_t s,
-                     int64_t* launches);
+                     const double* y, const uint32_t* perm, int M, float* yf, double* ys, double* f, DevStatus* st,
+                     cudaStream_t s, int64_t* launches);
+// refits of B value sets (MIXED operator): y (B x M doubles, node order)
+// through yo (M x B floats, node order), yT (the same in cell order) and fT
+// (M_Q x B floats) to f (B x M_Q doubles); B <= 256
+// (rows longer than 256 entries go to whole blocks: their list, from
+// list_long_rows at prepare time)
+void run_refit_apply_batch(int MQ, const uint32_t* rows, const uint32_t* col, const float* val, const double* y,
+                           const uint32_t* perm, int M, int B, float* yo, float* yT, float* fT, double* f,
+                           const uint32_t* long_list, const uint32_t* nlong, DevStatus* st, cudaStream_t s,
+                           int64_t* launches);
+void list_long_rows(int MQ, const uint32_t* rows, uint32_t* list, uint32_t* nlist, cudaStream_t s,
+                    int64_t* launches);
 int value_moment_count(int K);
 int mls_moment_slots(int K);
 
@@ -203,12 +218,11 @@ struct QuadArgs {
 };
 // part: 1 = ring FFT, 2 = Legendre contraction, 3 = both
 void run_quadrature(const QuadArgs& a, bool mixed, cudaStream_t s, int64_t* launches, int part = 3);
-// step 3 of B value sets (mixed form): ring FFTs of fgrid (B x M_Q, set b at
-// b M_Q) into F (B x (N+1)^2 complex FP32), the folded spectra G, and the
-// tensor-core Legendre contraction into coeffs (B x ncoef complex)
-cudaError_t run_quadrature_batch(const GridTables& g, const int* radices, int nrad, const double* fgrid, int B,
-                                 float2* F, float* G, const TcJob* jobs, int njobs, double* coeffs, unsigned* err,
-                                 cudaStream_t s, int64_t* launches);
+// step 3 of B value sets (mixed form), first part: ring FFTs of fgrid
+// (B x M_Q, set b at b M_Q) into F (B x (N+1)^2 complex FP32) and the folded
+// spectra split for 3xTF32 (Ghi, Glo); tc_legendre then contracts them
+cudaError_t run_spectra_batch(const GridTables& g, const int* radices, int nrad, const double* fgrid, int B,
+                              float2* F, float* Ghi, float* Glo, cudaStream_t s, int64_t* launches);
 
 // ---------------------------------------------------------------- voronoi.cu
 // Area of the spherical Voronoi cell of every point of g (FP32 area when

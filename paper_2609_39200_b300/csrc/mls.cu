@@ -617,7 +617,9 @@ __global__ void __launch_bounds__(128) gamma_kernel(MlsArgs a, SolveParams P, do
 
 // One warp per grid node: the members of its ball in the gather's order and
 // test, counted (FILL = false: rows[j], and the total) or written
-// (FILL = true: rows = CSR start; col = original node index, val = A_ji).
+// (FILL = true: rows = CSR start; col = the node's position in the plan's
+// cell order, val = A_ji). Columns in cell order keep the value reads of
+// neighbouring rows close together.
 template <int K, bool MIXED, bool FILL>
 __global__ void __launch_bounds__(128) op_rows_kernel(MlsArgs a, const double* __restrict__ gamma, uint32_t* rows,
                                                       uint32_t* __restrict__ col, void* valv,
@@ -674,7 +676,7 @@ __global__ void __launch_bounds__(128) op_rows_kernel(MlsArgs a, const double* _
         const unsigned bal = __ballot_sync(FULL, in);
         if (FILL && in) {
           const uint32_t e = pos + __popc(bal & below);
-          col[e] = a.nodes.perm[idx];
+          col[e] = idx;
           reinterpret_cast<float*>(valv)[e] = (float)entry((double)w, (double)u, (double)v);
         }
         pos += __popc(bal);
@@ -711,7 +713,7 @@ __global__ void __launch_bounds__(128) op_rows_kernel(MlsArgs a, const double* _
         const unsigned bal = __ballot_sync(FULL, in);
         if (FILL && in) {
           const uint32_t e = pos + __popc(bal & below);
-          col[e] = a.nodes.perm[idx];
+          col[e] = idx;
           reinterpret_cast<double*>(valv)[e] = entry(w, u, v);
         }
         pos += __popc(bal);
@@ -748,9 +750,15 @@ __global__ void __launch_bounds__(256) op_apply_kernel(int MQ, const uint32_t* _
   }
 }
 
-__global__ void to_float_kernel(const double* __restrict__ y, int n, float* __restrict__ yf) {
+// the values in the plan's cell order: ys[s] = y[perm[s]] (FP64) or
+// yf[s] = (float) y[perm[s]]
+__global__ void gather_values_kernel(const double* __restrict__ y, const uint32_t* __restrict__ perm, int n,
+                                     float* __restrict__ yf, double* __restrict__ ys) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) yf[i] = (float)y[i];
+  if (i >= n) return;
+  const double v = y[perm[i]];
+  if (yf) yf[i] = (float)v;
+  if (ys) ys[i] = v;
 }
 
 template <int K, bool MIXED>
@@ -788,17 +796,219 @@ void run_refit_operator(const MlsArgs& a, bool mixed, int part, double* gamma, u
 }
 
 void run_refit_apply(int MQ, bool mixed, const uint32_t* rows, const uint32_t* col, const void* val,
-                     const double* y, int M, float* yf, double* f, DevStatus* st, cudaStream_t s, int64_t* launches) {
+                     const double* y, const uint32_t* perm, int M, float* yf, double* ys, double* f, DevStatus* st,
+                     cudaStream_t s, int64_t* launches) {
   const int cap = current_sm_count() * 64;
   const int blocks = (MQ + 7) / 8 < cap ? (MQ + 7) / 8 : cap;
   if (mixed) {
-    to_float_kernel<<<(M + 255) / 256, 256, 0, s>>>(y, M, yf);
+    gather_values_kernel<<<(M + 255) / 256, 256, 0, s>>>(y, perm, M, yf, nullptr);
     op_apply_kernel<float><<<blocks, 256, 0, s>>>(MQ, rows, col, reinterpret_cast<const float*>(val), yf, f, st);
-    *launches += 2;
   } else {
-    op_apply_kernel<double><<<blocks, 256, 0, s>>>(MQ, rows, col, reinterpret_cast<const double*>(val), y, f, st);
-    ++*launches;
+    gather_values_kernel<<<(M + 255) / 256, 256, 0, s>>>(y, perm, M, nullptr, ys);
+    op_apply_kernel<double><<<blocks, 256, 0, s>>>(MQ, rows, col, reinterpret_cast<const double*>(val), ys, f, st);
   }
+  *launches += 2;
+}
+
+// ---------------------------------------------- refits of many value sets
+// The same operator applied to B value sets: y (B x M doubles, set b at b M)
+// is transposed to M x B floats (the B values of one node contiguous) and its
+// rows gathered into the plan's cell order (yT; the operator's columns),
+// one warp per grid node walks its row once and every lane accumulates the
+// sets b = lane, lane + 32, ... (each entry's B values are one coalesced
+// read), giving fT (M_Q x B floats), transposed again to the B grids the
+// batched step 3 takes (B x M_Q doubles).
+__global__ void __launch_bounds__(256) to_float_t_kernel(const double* __restrict__ y, int B, int M,
+                                                         float* __restrict__ yT) {
+  __shared__ float t[32][33];
+  const int i0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int b = b0 + r, i = i0 + tx;
+    t[r][tx] = (b < B && i < M) ? (float)y[(size_t)b * M + i] : 0.f;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r, b = b0 + tx;
+    if (i < M && b < B) yT[(size_t)i * B + b] = t[tx][r];
+  }
+}
+
+// rows of B floats gathered into the plan's cell order: yT[s] = yo[perm[s]]
+// (blocks of 32 sets x 8 rows)
+__global__ void __launch_bounds__(256) gather_rows_kernel(const float* __restrict__ yo, const uint32_t* __restrict__ perm,
+                                                          int M, int B, float* __restrict__ yT) {
+  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int b = blockIdx.y * 32 + (threadIdx.x & 31);
+  if (r >= M || b >= B) return;
+  yT[(size_t)r * B + b] = yo[(size_t)perm[r] * B + b];
+}
+
+// Rows of more than OP_LONG entries (grid nodes at the centre of a hole of
+// the node set collect tens of thousands) are taken by whole blocks
+// (op_apply_batch_long_kernel); the others by one warp each.
+constexpr uint32_t OP_LONG = 256;
+
+// the entries [e0, e1) of one row for the sets b = lane + 32 q
+template <int BL>
+__device__ __forceinline__ void op_row_part(const uint32_t* __restrict__ col, const float* __restrict__ val,
+                                            const float* __restrict__ yT, int B, uint32_t e0, uint32_t e1,
+                                            uint32_t step, float (&acc)[BL]) {
+  const int lane = threadIdx.x & 31;
+  for (uint32_t base = e0; base < e1; base += step) {
+    const uint32_t e = base + lane;
+    const uint32_t cl = e < e1 ? col[e] : 0u;
+    const float vl = e < e1 ? val[e] : 0.f;
+    const int cnt = (int)min(32u, e1 - base);
+    for (int i = 0; i < cnt; i += 8) {
+      float yv[8][BL];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const uint32_t c = __shfl_sync(FULL, cl, (i + u) & 31);
+        const float* yr = yT + (size_t)c * B;
+#pragma unroll
+        for (int q = 0; q < BL; ++q) {
+          const int b = lane + 32 * q;
+          yv[u][q] = (i + u < cnt && b < B) ? yr[b] : 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float v = __shfl_sync(FULL, vl, (i + u) & 31);
+#pragma unroll
+        for (int q = 0; q < BL; ++q) acc[q] = fmaf(v, yv[u][q], acc[q]);
+      }
+    }
+  }
+}
+
+template <int BL>
+__global__ void __launch_bounds__(256) op_apply_batch_long_kernel(const uint32_t* __restrict__ list,
+                                                                  const uint32_t* __restrict__ nlist,
+                                                                  const uint32_t* __restrict__ rows,
+                                                                  const uint32_t* __restrict__ col,
+                                                                  const float* __restrict__ val,
+                                                                  const float* __restrict__ yT, int B,
+                                                                  float* __restrict__ fT, DevStatus* st) {
+  __shared__ float part[8][BL * 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t n = *nlist;
+  for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) {
+    const uint32_t j = list[t];
+    const uint32_t e0 = rows[j], e1 = rows[j + 1];
+    float acc[BL];
+#pragma unroll
+    for (int q = 0; q < BL; ++q) acc[q] = 0.f;
+    // warp w takes the 32-entry chunks w, w + 8, ... of the row
+    op_row_part<BL>(col, val, yT, B, e0 + 32 * warp, e1, 256, acc);
+#pragma unroll
+    for (int q = 0; q < BL; ++q) part[warp][lane + 32 * q] = acc[q];
+    __syncthreads();
+    // the eight partial sums of every set, added in warp order
+    if (warp == 0) {
+      bool bad = false;
+#pragma unroll
+      for (int q = 0; q < BL; ++q) {
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) sum += part[w][lane + 32 * q];
+        const int b = lane + 32 * q;
+        if (b < B) {
+          if (!isfinite(sum)) bad = true;
+          fT[(size_t)j * B + b] = sum;
+        }
+      }
+      if (__any_sync(FULL, bad) && lane == 0) set_flag(st, ST_NONFINITE);
+    }
+    __syncthreads();
+  }
+}
+
+// the rows of more than OP_LONG entries, listed (their count in *nlist)
+__global__ void op_long_rows_kernel(int MQ, const uint32_t* __restrict__ rows, uint32_t* __restrict__ list,
+                                    uint32_t* nlist) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < MQ && rows[j + 1] - rows[j] > OP_LONG) list[atomicAdd(nlist, 1u)] = (uint32_t)j;
+}
+
+template <int BL>
+__global__ void __launch_bounds__(256) op_apply_batch_kernel(int MQ, const uint32_t* __restrict__ rows,
+                                                             const uint32_t* __restrict__ col,
+                                                             const float* __restrict__ val,
+                                                             const float* __restrict__ yT, int B,
+                                                             float* __restrict__ fT, DevStatus* st) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  bool bad = false;
+  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < MQ; j += nw) {
+    const uint32_t e0 = rows[j], e1 = rows[j + 1];
+    if (e1 - e0 > OP_LONG) continue;          // a block takes it
+    float acc[BL];
+#pragma unroll
+    for (int q = 0; q < BL; ++q) acc[q] = 0.f;
+    // 32 entries at a time (one coalesced load of columns and entries), then
+    // their value rows eight at a time, all eight gathers in flight at once
+    op_row_part<BL>(col, val, yT, B, e0, e1, 32, acc);
+#pragma unroll
+    for (int q = 0; q < BL; ++q) {
+      const int b = lane + 32 * q;
+      if (b < B) {
+        if (!isfinite(acc[q])) bad = true;
+        fT[(size_t)j * B + b] = acc[q];
+      }
+    }
+  }
+  if (__any_sync(FULL, bad) && lane == 0) set_flag(st, ST_NONFINITE);
+}
+
+__global__ void __launch_bounds__(256) from_float_t_kernel(const float* __restrict__ fT, int MQ, int B,
+                                                           double* __restrict__ f) {
+  __shared__ float t[32][33];
+  const int j0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int j = j0 + r, b = b0 + tx;
+    t[r][tx] = (j < MQ && b < B) ? fT[(size_t)j * B + b] : 0.f;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int b = b0 + r, j = j0 + tx;
+    if (b < B && j < MQ) f[(size_t)b * MQ + j] = (double)t[tx][r];
+  }
+}
+
+void list_long_rows(int MQ, const uint32_t* rows, uint32_t* list, uint32_t* nlist, cudaStream_t s,
+                    int64_t* launches) {
+  cudaMemsetAsync(nlist, 0, sizeof(uint32_t), s);
+  op_long_rows_kernel<<<(MQ + 255) / 256, 256, 0, s>>>(MQ, rows, list, nlist);
+  ++*launches;
+}
+
+void run_refit_apply_batch(int MQ, const uint32_t* rows, const uint32_t* col, const float* val, const double* y,
+                           const uint32_t* perm, int M, int B, float* yo, float* yT, float* fT, double* f,
+                           const uint32_t* long_list, const uint32_t* nlong, DevStatus* st, cudaStream_t s,
+                           int64_t* launches) {
+  to_float_t_kernel<<<dim3((M + 31) / 32, (B + 31) / 32), 256, 0, s>>>(y, B, M, yo);
+  gather_rows_kernel<<<dim3((M + 7) / 8, (B + 31) / 32), 256, 0, s>>>(yo, perm, M, B, yT);
+  const int cap = current_sm_count() * 64;
+  const int blocks = (MQ + 7) / 8 < cap ? (MQ + 7) / 8 : cap;
+  const int lblocks = current_sm_count() * 4;
+#define HAMLS_OP_BATCH(BLV)                                                                               \
+  op_apply_batch_kernel<BLV><<<blocks, 256, 0, s>>>(MQ, rows, col, val, yT, B, fT, st);                     \
+  op_apply_batch_long_kernel<BLV><<<lblocks, 256, 0, s>>>(long_list, nlong, rows, col, val, yT, B, fT, st)
+  if (B <= 32) {
+    HAMLS_OP_BATCH(1);
+  } else if (B <= 64) {
+    HAMLS_OP_BATCH(2);
+  } else if (B <= 128) {
+    HAMLS_OP_BATCH(4);
+  } else {
+    HAMLS_OP_BATCH(8);
+  }
+#undef HAMLS_OP_BATCH
+  ++*launches;
+  from_float_t_kernel<<<dim3((MQ + 31) / 32, (B + 31) / 32), 256, 0, s>>>(fT, MQ, B, f);
+  *launches += 4;
 }
 
 int value_moment_count(int K) { return (K + 1) * (K + 2) / 2; }

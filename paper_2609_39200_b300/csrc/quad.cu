@@ -37,12 +37,14 @@ __global__ void __launch_bounds__(256) ring_fft_kernel(const double* __restrict_
   const int L = 2 * N + 2;
   cT* buf0 = reinterpret_cast<cT*>(smem_raw);
   cT* buf1 = buf0 + L;
+  cT* sW = buf1 + L;                        // the twiddles, read many times per stage
   const int ra = 2 * blockIdx.x, rb = ra + 1;
   const bool hasb = rb <= N;
   // value set blockIdx.y of a batch: grids M_Q apart, spectra (N+1)^2 apart
   f += (size_t)blockIdx.y * (size_t)(N + 1) * L;
   F += (size_t)blockIdx.y * (size_t)(N + 1) * (N + 1);
   for (int j = threadIdx.x; j < L; j += blockDim.x) {
+    sW[j] = W[j];
     T x = (T)f[(size_t)ra * L + j];
     T y = hasb ? (T)f[(size_t)rb * L + j] : T(0);
     buf0[j].x = x;
@@ -57,6 +59,40 @@ __global__ void __launch_bounds__(256) ring_fft_kernel(const double* __restrict_
     const int T_ = L / R;
     const int NsR = Ns * R;
     const int strideA = L / NsR, strideB = L / R;
+    if (R <= 32) {
+      // one butterfly per thread: group g = (hi, jl) reads in[j + q T_] for
+      // q < R and writes out[hi Ns R + jl + r Ns] for r < R (one division per
+      // group); twiddle exponents q (jl strideA + r strideB) advance by
+      // additions mod L
+      for (int g = threadIdx.x; g < T_; g += blockDim.x) {
+        const int hi = g / Ns, jl = g - hi * Ns;
+        const int j = hi * Ns + jl;
+        const int base = hi * NsR + jl;
+        int step = jl * strideA;             // exponent step of output r, mod L
+        for (int r = 0; r < R; ++r) {
+          int e = 0;
+          T ax = 0, ay = 0;
+          for (int q = 0; q < R; ++q) {
+            const cT v = in[j + q * T_];
+            const cT w = sW[e];
+            ax += v.x * w.x - v.y * w.y;
+            ay += v.x * w.y + v.y * w.x;
+            e += step;
+            if (e >= L) e -= L;
+          }
+          out[base + r * Ns].x = ax;
+          out[base + r * Ns].y = ay;
+          step += strideB;
+          if (step >= L) step -= L;
+        }
+      }
+      __syncthreads();
+      cT* t = in;
+      in = out;
+      out = t;
+      Ns *= R;
+      continue;
+    }
     for (int o = threadIdx.x; o < L; o += blockDim.x) {
       const int hi = o / NsR, rem = o - hi * NsR;
       const int r = rem / Ns, jl = rem - r * Ns;
@@ -67,7 +103,7 @@ __global__ void __launch_bounds__(256) ring_fft_kernel(const double* __restrict_
       T ax = 0, ay = 0;
       for (int q = 0; q < R; ++q) {
         const cT v = in[j + q * T_];
-        const cT w = W[e];
+        const cT w = sW[e];
         ax += v.x * w.x - v.y * w.y;
         ay += v.x * w.y + v.y * w.x;
         e += step;
@@ -171,7 +207,7 @@ static void launch_quad(const QuadArgs& a, const typename C2<T>::t* W, const T* 
                         int64_t* launches, int part) {
   using cT = typename C2<T>::t;
   const int N = a.g->N, L = 2 * N + 2, hc = a.g->hc;
-  const size_t smem_fft = 2 * (size_t)L * sizeof(cT);
+  const size_t smem_fft = 3 * (size_t)L * sizeof(cT);
   const size_t smem_leg = 2 * (size_t)hc * sizeof(cT);
   static unsigned done_fft = 0, done_leg = 0;   // per device
   set_smem_attr_once((const void*)ring_fft_kernel<T>, 200 * 1024, &done_fft);
@@ -194,8 +230,10 @@ static void launch_quad(const QuadArgs& a, const typename C2<T>::t* W, const T* 
 //   E = F_c(m) + F_{N-c}(m),  O = F_c(m) - F_{N-c}(m)   (E = O = F_c(m) if c = N - c),
 // stored as G[(2m + p) * 2B + 2b + {0: re, 1: im}][c], p = 0 for E, 1 for O.
 // A 32 x 32 tile of (c, m) per block: reads along m, writes along c.
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
 __global__ void __launch_bounds__(256) fold_spectra_kernel(const float2* __restrict__ F, int N, int hc, int hcp,
-                                                           int B, float* __restrict__ G) {
+                                                           int B, float* __restrict__ Ghi, float* __restrict__ Glo) {
   __shared__ float2 E[32][33], O[32][33];
   const int b = blockIdx.z, m0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   const float2* Fb = F + (size_t)b * (N + 1) * (N + 1);
@@ -222,18 +260,35 @@ __global__ void __launch_bounds__(256) fold_spectra_kernel(const float2* __restr
   for (int r = ty; r < 32; r += 8) {
     const int m = m0 + r, c = c0 + tx;
     if (m > N || c >= hc) continue;
-    float* ge = G + (size_t)(2 * m) * ps + (size_t)(2 * b) * rs + c;
-    float* go = ge + ps;
-    ge[0] = E[r][tx].x;
-    ge[rs] = E[r][tx].y;
-    go[0] = O[r][tx].x;
-    go[rs] = O[r][tx].y;
+    const size_t o = (size_t)(2 * m) * ps + (size_t)(2 * b) * rs + c;
+    const float v[4] = {E[r][tx].x, E[r][tx].y, O[r][tx].x, O[r][tx].y};
+    const size_t at[4] = {o, o + rs, o + ps, o + ps + rs};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float hi = tf32_hi(v[q]);
+      Ghi[at[q]] = hi;
+      Glo[at[q]] = v[q] - hi;
+    }
   }
 }
 
-cudaError_t run_quadrature_batch(const GridTables& g, const int* radices, int nrad, const double* fgrid, int B,
-                                 float2* F, float* G, const TcJob* jobs, int njobs, double* coeffs, unsigned* err,
-                                 cudaStream_t s, int64_t* launches) {
+__global__ void split_tf32_kernel(const float* __restrict__ x, size_t n, float* __restrict__ hi,
+                                  float* __restrict__ lo) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float h = tf32_hi(x[i]);
+    hi[i] = h;
+    lo[i] = x[i] - h;
+  }
+}
+
+void split_tf32(const float* x, size_t n, float* hi, float* lo, cudaStream_t s, int64_t* launches) {
+  const size_t blocks = (n + 255) / 256;
+  split_tf32_kernel<<<(int)(blocks < 65535 ? blocks : 65535), 256, 0, s>>>(x, n, hi, lo);
+  ++*launches;
+}
+
+cudaError_t run_spectra_batch(const GridTables& g, const int* radices, int nrad, const double* fgrid, int B,
+                              float2* F, float* Ghi, float* Glo, cudaStream_t s, int64_t* launches) {
   const int N = g.N, L = 2 * N + 2;
   QuadArgs qa;
   memset(&qa, 0, sizeof(qa));
@@ -242,12 +297,11 @@ cudaError_t run_quadrature_batch(const GridTables& g, const int* radices, int nr
   qa.nrad = nrad;
   static unsigned done_fft = 0;
   set_smem_attr_once((const void*)ring_fft_kernel<float>, 200 * 1024, &done_fft);
-  ring_fft_kernel<float><<<dim3((N + 2) / 2, B), 256, 2 * (size_t)L * sizeof(float2), s>>>(fgrid, N, qa, g.W32, F);
-  fold_spectra_kernel<<<dim3((N + 1 + 31) / 32, (g.hc + 31) / 32, B), 256, 0, s>>>(F, N, g.hc, g.hcp, B, G);
+  ring_fft_kernel<float><<<dim3((N + 2) / 2, B), 256, 3 * (size_t)L * sizeof(float2), s>>>(fgrid, N, qa, g.W32, F);
+  fold_spectra_kernel<<<dim3((N + 1 + 31) / 32, (g.hc + 31) / 32, B), 256, 0, s>>>(F, N, g.hc, g.hcp, B, Ghi,
+                                                                                    Glo);
   *launches += 2;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return tc_legendre(g, G, B, jobs, njobs, coeffs, err, s, launches);
+  return cudaGetLastError();
 }
 
 void run_quadrature(const QuadArgs& a, bool mixed, cudaStream_t s, int64_t* launches, int part) {

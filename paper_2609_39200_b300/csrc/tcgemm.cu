@@ -137,28 +137,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // ------------------------------------------------------------ the kernel
-// split the FP32 tile at p (n elements) into hi (in place) and lo
-__device__ __forceinline__ void split_tile(float* p, float* lo, int n) {
-  float4* p4 = reinterpret_cast<float4*>(p);
-  float4* l4 = reinterpret_cast<float4*>(lo);
-  for (int i = threadIdx.x; i < n / 4; i += TC_THREADS) {
-    float4 x = p4[i], h, l;
-    h.x = __uint_as_float(__float_as_uint(x.x) & 0xFFFFE000u);
-    h.y = __uint_as_float(__float_as_uint(x.y) & 0xFFFFE000u);
-    h.z = __uint_as_float(__float_as_uint(x.z) & 0xFFFFE000u);
-    h.w = __uint_as_float(__float_as_uint(x.w) & 0xFFFFE000u);
-    l.x = x.x - h.x;
-    l.y = x.y - h.y;
-    l.z = x.z - h.z;
-    l.w = x.w - h.w;
-    p4[i] = h;
-    l4[i] = l;
-  }
-}
+// The main loop runs on one thread: per K step it waits for the stage's four
+// tiles (A hi, A lo, B hi, B lo), issues the 4 x 3 products and commits them
+// to the stage's "empty" barrier, then refills the stage two steps ahead once
+// the products have read it. The other threads wait for the final commit.
+// The result goes from tensor memory to shared memory (transposed: column n
+// of D at S + n * TC_LDS) and the epilogue writes it out from there.
+constexpr int TC_LDS = 129;
 
 template <class Epi>
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
-                                                                 const __grid_constant__ CUtensorMap mapB,
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapAh,
+                                                                 const __grid_constant__ CUtensorMap mapAl,
+                                                                 const __grid_constant__ CUtensorMap mapBh,
+                                                                 const __grid_constant__ CUtensorMap mapBl,
                                                                  const TcJob* __restrict__ jobs, int K, Epi epi,
                                                                  unsigned* err) {
   extern __shared__ unsigned char tc_raw[];
@@ -175,7 +166,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
   job.a_y += 128 * (int)blockIdx.y;
   const int KT = (K + TC_BK - 1) / TC_BK;
   const int nb = job.nt / TC_BOX;
-  const uint32_t stage_bytes = (uint32_t)(128 / TC_BOX + nb) * TC_BOX * TC_BK * 4;
+  const uint32_t stage_bytes = 2u * (uint32_t)(128 / TC_BOX + nb) * TC_BOX * TC_BK * 4;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
@@ -191,47 +182,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     mbar_init(done, 1);
     *bad = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    prefetch_map(&mapA);
-    prefetch_map(&mapB);
+    prefetch_map(&mapAh);
+    prefetch_map(&mapAl);
+    prefetch_map(&mapBh);
+    prefetch_map(&mapBl);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  auto sA = [&](int s) { return reinterpret_cast<float*>(sm + s * TC_STAGE); };
-  auto sAlo = [&](int s) { return reinterpret_cast<float*>(sm + s * TC_STAGE + TC_TILE_A); };
-  auto sB = [&](int s) { return reinterpret_cast<float*>(sm + s * TC_STAGE + 2 * TC_TILE_A); };
-  auto sBlo = [&](int s) { return reinterpret_cast<float*>(sm + s * TC_STAGE + 2 * TC_TILE_A + TC_TILE_B); };
-  auto issue = [&](int kt, int s) {
-    mbar_expect_tx(&full[s], stage_bytes);
-    for (int r = 0; r < 128 / TC_BOX; ++r)
-      tma_load_3d(sA(s) + r * TC_BOX * TC_BK, &mapA, kt * TC_BK, job.a_y + r * TC_BOX, job.a_z, &full[s]);
-    for (int r = 0; r < nb; ++r)
-      tma_load_3d(sB(s) + r * TC_BOX * TC_BK, &mapB, kt * TC_BK, job.b_y + r * TC_BOX, 0, &full[s]);
-  };
-  int loads[2] = {0, 0};    // TMA loads issued per stage (thread 0)
+  // lanes 1..31 of warp 0 park at the warp barrier below (not spinning on
+  // the mbarrier beside the thread that drives the pipeline)
   if (tid == 0) {
+    auto tile = [&](int s, int which) { return sm + s * TC_STAGE + which * TC_TILE_A; };   // A hi, A lo
+    auto tileB = [&](int s, int which) { return sm + s * TC_STAGE + 2 * TC_TILE_A + which * TC_TILE_B; };
+    auto issue = [&](int kt, int s) {
+      mbar_expect_tx(&full[s], stage_bytes);
+      for (int r = 0; r < 128 / TC_BOX; ++r) {
+        tma_load_3d(tile(s, 0) + r * TC_BOX * TC_BK * 4, &mapAh, kt * TC_BK, job.a_y + r * TC_BOX, job.a_z, &full[s]);
+        tma_load_3d(tile(s, 1) + r * TC_BOX * TC_BK * 4, &mapAl, kt * TC_BK, job.a_y + r * TC_BOX, job.a_z, &full[s]);
+      }
+      for (int r = 0; r < nb; ++r) {
+        tma_load_3d(tileB(s, 0) + r * TC_BOX * TC_BK * 4, &mapBh, kt * TC_BK, job.b_y + r * TC_BOX, 0, &full[s]);
+        tma_load_3d(tileB(s, 1) + r * TC_BOX * TC_BK * 4, &mapBl, kt * TC_BK, job.b_y + r * TC_BOX, 0, &full[s]);
+      }
+    };
+    int loads[2] = {0, 0};
     for (int kt = 0; kt < KT && kt < 2; ++kt) {
       issue(kt, kt);
       ++loads[kt];
     }
-  }
-  const uint32_t idesc = tf32_idesc(job.nt);
-  for (int kt = 0; kt < KT; ++kt) {
-    const int s = kt & 1;
-    const uint32_t ph = (uint32_t)(kt >> 1) & 1u;
-    if (!mbar_wait(&full[s], ph)) atomicExch(bad, 1);
-    __syncthreads();
-    if (*bad) break;
-    split_tile(sA(s), sAlo(s), 128 * TC_BK);
-    split_tile(sB(s), sBlo(s), job.nt * TC_BK);
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
+    const uint32_t idesc = tf32_idesc(job.nt);
+    bool ok = true;
+    for (int kt = 0; kt < KT && ok; ++kt) {
+      const int s = kt & 1;
+      const uint32_t ph = (uint32_t)(kt >> 1) & 1u;
+      if (!mbar_wait(&full[s], ph)) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
-      const uint32_t a_hi = smem_addr(sA(s)), a_lo = smem_addr(sAlo(s));
-      const uint32_t b_hi = smem_addr(sB(s)), b_lo = smem_addr(sBlo(s));
+      const uint32_t a_hi = smem_addr(tile(s, 0)), a_lo = smem_addr(tile(s, 1));
+      const uint32_t b_hi = smem_addr(tileB(s, 0)), b_lo = smem_addr(tileB(s, 1));
 #pragma unroll
       for (int k = 0; k < TC_BK / 8; ++k) {
         // K = 8 TF32 per product: 32 bytes further along the swizzled row
@@ -245,39 +238,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       if (kt + 2 < KT) {
         // the stage is free once these products have read it
         if (!mbar_wait(&empty[s], ph)) {
-          atomicExch(bad, 1);
-        } else {
-          issue(kt + 2, s);
-          ++loads[s];
+          ok = false;
+          break;
         }
+        issue(kt + 2, s);
+        ++loads[s];
       }
     }
+    // the final commit covers every product issued
+    mma_commit(done);
+    if (!ok) {
+      *bad = 1;
+      // wait (bounded) for every stage still loading before the CTA may exit
+      for (int s = 0; s < 2; ++s)
+        if (loads[s] > 0) (void)mbar_wait(&full[s], (uint32_t)(loads[s] - 1) & 1u);
+    }
   }
-  // drain: every product issued has finished (and, after an error, every
-  // copy issued has landed: the last load of each stage completes that
-  // stage's phase (loads - 1))
-  if (tid == 0) mma_commit(done);
-  __syncthreads();
+  if (warp == 0) __syncwarp();
   if (!mbar_wait(done, 0)) atomicExch(bad, 1);
-  if (tid == 0 && *bad) {
-    for (int s = 0; s < 2; ++s)
-      if (loads[s] > 0) (void)mbar_wait(&full[s], (uint32_t)(loads[s] - 1) & 1u);
-  }
-  __syncthreads();
   tc_fence_after();
-  if (!*bad) {
+  __syncthreads();
+  const bool ok = *bad == 0;
+  float* S = reinterpret_cast<float*>(sm);
+  if (ok) {
     // warp w reads lanes 32w..32w+31 of D: rows 32w + lane of the tile
     const int row = warp * 32 + lane;
     for (int c0 = 0; c0 < job.nt; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      epi(job, row, c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) S[(c0 + i) * TC_LDS + row] = v[i];
     }
   } else if (tid == 0) {
     atomicOr(err, 1u);
   }
   tc_fence_before();
   __syncthreads();
+  if (ok) epi.store(job, S, tid);
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_MAXN) : "memory");
@@ -321,11 +318,12 @@ bool tc_make_map(CUtensorMap* map, const float* base, uint64_t d0, uint64_t d1, 
 }
 
 template <class Epi>
-static cudaError_t tc_launch(const CUtensorMap& mA, const CUtensorMap& mB, const TcJob* jobs, int njobs, int mtiles,
-                             int K, const Epi& epi, unsigned* err, cudaStream_t s) {
+static cudaError_t tc_launch(const CUtensorMap* maps, const TcJob* jobs, int njobs, int mtiles, int K, const Epi& epi,
+                             unsigned* err, cudaStream_t s) {
   static unsigned done = 0;
   set_smem_attr_once((const void*)tc_gemm_kernel<Epi>, TC_SMEM, &done);
-  tc_gemm_kernel<Epi><<<dim3(njobs, mtiles), TC_THREADS, TC_SMEM, s>>>(mA, mB, jobs, K, epi, err);
+  tc_gemm_kernel<Epi><<<dim3(njobs, mtiles), TC_THREADS, TC_SMEM, s>>>(maps[0], maps[1], maps[2], maps[3], jobs, K,
+                                                                       epi, err);
   return cudaGetLastError();
 }
 
@@ -337,19 +335,20 @@ struct EpiLegendre {
   double* coeffs;
   int N, rows;            // rows of D that exist: 2 B
   size_t ncoef;
-  __device__ void operator()(const TcJob& j, int row, int c0, const float* v) const {
-    const int r = j.a_y + row;
-    if (r >= rows) return;
-    const int b = r >> 1, ri = r & 1, m = j.e0;
-    double* out = coeffs + (size_t)b * ncoef * 2 + ri;
+  // thread t takes (set, column) pairs with the column fastest: a set's
+  // coefficients of one order and parity lie 32 bytes apart
+  __device__ void store(const TcJob& j, const float* S, int tid) const {
+    const int m = j.e0;
     const size_t row0 = (size_t)m * (N + 1) - (size_t)m * (m - 1) / 2;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int jj = j.e2 + c0 + i;
-      if (c0 + i < j.nt && jj < j.e3) {
-        const int l = m + j.e1 + 2 * jj;
-        out[2 * (row0 + (size_t)(l - m))] = (double)v[i];
-      }
+    const int sets = 64;                           // 128 rows of D: 64 sets
+    for (int idx = tid; idx < sets * j.nt; idx += TC_THREADS) {
+      const int bl = idx / j.nt, c = idx - bl * j.nt;
+      const int r = j.a_y + 2 * bl;
+      const int jj = j.e2 + c;
+      if (r >= rows || jj >= j.e3) continue;
+      const int l = m + j.e1 + 2 * jj;
+      double2* out = reinterpret_cast<double2*>(coeffs) + (size_t)(r >> 1) * ncoef + row0 + (size_t)(l - m);
+      *out = make_double2((double)S[c * TC_LDS + 2 * bl], (double)S[c * TC_LDS + 2 * bl + 1]);
     }
   }
 };
@@ -382,20 +381,22 @@ int tc_legendre_jobs(int N, TcJob* out) {
   return n;
 }
 
-cudaError_t tc_legendre(const GridTables& g, const float* G, int B, const TcJob* jobs, int njobs, double* coeffs,
-                        unsigned* err, cudaStream_t s, int64_t* launches) {
+cudaError_t tc_legendre(const GridTables& g, const float* Ghi, const float* Glo, int B, const TcJob* jobs, int njobs,
+                        double* coeffs, unsigned* err, cudaStream_t s, int64_t* launches) {
   const int N = g.N;
   const uint64_t ncoef = (uint64_t)(N + 1) * (N + 2) / 2;
-  CUtensorMap mA, mB;
-  memset(&mA, 0, sizeof(mA));
-  memset(&mB, 0, sizeof(mB));
+  CUtensorMap maps[4];
+  memset(maps, 0, sizeof(maps));
   const uint64_t ld = (uint64_t)g.hcp * 4;
-  if (!tc_make_map(&mA, G, (uint64_t)g.hc, (uint64_t)(2 * B), (uint64_t)(2 * (N + 1)), ld, ld * 2 * B) ||
-      !tc_make_map(&mB, g.A32, (uint64_t)g.hc, ncoef, 1, ld, ld * ncoef))
+  const uint64_t zs = (uint64_t)2 * (N + 1);
+  if (!tc_make_map(&maps[0], Ghi, (uint64_t)g.hc, (uint64_t)(2 * B), zs, ld, ld * 2 * B) ||
+      !tc_make_map(&maps[1], Glo, (uint64_t)g.hc, (uint64_t)(2 * B), zs, ld, ld * 2 * B) ||
+      !tc_make_map(&maps[2], g.A32hi, (uint64_t)g.hc, ncoef, 1, ld, ld * ncoef) ||
+      !tc_make_map(&maps[3], g.A32lo, (uint64_t)g.hc, ncoef, 1, ld, ld * ncoef))
     return cudaErrorInvalidValue;
   EpiLegendre epi{coeffs, N, 2 * B, (size_t)ncoef};
   ++*launches;
-  return tc_launch(mA, mB, jobs, njobs, (2 * B + 127) / 128, g.hc, epi, err, s);
+  return tc_launch(maps, jobs, njobs, (2 * B + 127) / 128, g.hc, epi, err, s);
 }
 
 // ------------------------------------------------------------ debug GEMM
@@ -403,13 +404,11 @@ cudaError_t tc_legendre(const GridTables& g, const float* G, int B, const TcJob*
 struct EpiDense {
   float* C;
   int M, N, ldc;
-  __device__ void operator()(const TcJob& j, int row, int c0, const float* v) const {
-    const int r = j.a_y + row;
-    if (r >= M) return;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int c = j.b_y + c0 + i;
-      if (c0 + i < j.nt && c < N) C[(size_t)r * ldc + c] = v[i];
+  __device__ void store(const TcJob& j, const float* S, int tid) const {
+    for (int idx = tid; idx < 128 * j.nt; idx += TC_THREADS) {
+      const int row = idx / j.nt, c = idx - row * j.nt;
+      const int r = j.a_y + row, cc = j.b_y + c;
+      if (r < M && cc < N) C[(size_t)r * ldc + cc] = S[c * TC_LDS + row];
     }
   }
 };
@@ -421,12 +420,6 @@ using namespace hamls;
 extern "C" hamls_status hamls_debug_tc_gemm(const float* A, const float* B, float* C, int M, int N, int K,
                                             cudaStream_t stream) {
   if (!A || !B || !C || M < 1 || N < 1 || K < 1 || (K % 4)) return HAMLS_ERR_INVALID_ARG;
-  CUtensorMap mA, mB;
-  memset(&mA, 0, sizeof(mA));
-  memset(&mB, 0, sizeof(mB));
-  if (!tc_make_map(&mA, A, (uint64_t)K, (uint64_t)M, 1, (uint64_t)K * 4, (uint64_t)K * 4 * M) ||
-      !tc_make_map(&mB, B, (uint64_t)K, (uint64_t)N, 1, (uint64_t)K * 4, (uint64_t)K * 4 * N))
-    return HAMLS_ERR_INVALID_ARG;
   // jobs: 128-row tiles of A times 256-column tiles of B (the last ones
   // rounded up to 32 columns)
   const int mt = (M + 127) / 128;
@@ -443,19 +436,41 @@ extern "C" hamls_status hamls_debug_tc_gemm(const float* A, const float* B, floa
       const int cols = N - j.b_y < TC_MAXN ? N - j.b_y : TC_MAXN;
       j.nt = (cols + 31) / 32 * 32;
     }
-  TcJob* dj = nullptr;
-  unsigned* derr = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&dj, sizeof(TcJob) * njobs + 16, stream);
+  // the operands split into hi and lo on the device (scratch for this call)
+  const size_t na = (size_t)M * K, nbk = (size_t)N * K;
+  auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t bj = up(sizeof(TcJob) * njobs + 16), ba = up(na * 4), bb = up(nbk * 4);
+  char* mem = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&mem, bj + 2 * ba + 2 * bb, stream);
+  TcJob* dj = reinterpret_cast<TcJob*>(mem);
+  unsigned* derr = reinterpret_cast<unsigned*>(mem + sizeof(TcJob) * njobs);
+  float* Ah = reinterpret_cast<float*>(mem + bj);
+  float* Al = reinterpret_cast<float*>(mem + bj + ba);
+  float* Bh = reinterpret_cast<float*>(mem + bj + 2 * ba);
+  float* Bl = reinterpret_cast<float*>(mem + bj + 2 * ba + bb);
+  int64_t launches = 0;
+  CUtensorMap maps[4];
+  memset(maps, 0, sizeof(maps));
   if (e == cudaSuccess) e = cudaMemcpyAsync(dj, hj, sizeof(TcJob) * njobs, cudaMemcpyHostToDevice, stream);
-  derr = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(dj) + sizeof(TcJob) * njobs);
   if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, 4, stream);
+  if (e == cudaSuccess) {
+    split_tf32(A, na, Ah, Al, stream, &launches);
+    split_tf32(B, nbk, Bh, Bl, stream, &launches);
+    const uint64_t ld = (uint64_t)K * 4;
+    if (!tc_make_map(&maps[0], Ah, (uint64_t)K, (uint64_t)M, 1, ld, ld * M) ||
+        !tc_make_map(&maps[1], Al, (uint64_t)K, (uint64_t)M, 1, ld, ld * M) ||
+        !tc_make_map(&maps[2], Bh, (uint64_t)K, (uint64_t)N, 1, ld, ld * N) ||
+        !tc_make_map(&maps[3], Bl, (uint64_t)K, (uint64_t)N, 1, ld, ld * N))
+      e = cudaErrorInvalidValue;
+  }
   EpiDense epi{C, M, N, N};
-  if (e == cudaSuccess) e = tc_launch(mA, mB, dj, njobs, 1, K, epi, derr, stream);
+  if (e == cudaSuccess) e = tc_launch(maps, dj, njobs, 1, K, epi, derr, stream);
   unsigned herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-  if (dj) cudaFreeAsync(dj, stream);
+  if (mem) cudaFreeAsync(mem, stream);
   delete[] hj;
+  if (e == cudaErrorInvalidValue) return HAMLS_ERR_INVALID_ARG;
   if (e != cudaSuccess) return HAMLS_ERR_CUDA;
   return herr ? HAMLS_ERR_TIMEOUT : HAMLS_OK;
 }
