@@ -99,9 +99,10 @@ struct hamls_plan_s {
   unsigned* batch_err = nullptr;
   // scattered nodes: the cell structure (B bands, P cells per band) follows
   // the current node count; Bcap is the largest one the arena holds
-  int B = 0, P = 0, Bcap = 0, edge_B = 0;
+  int B = 0, P = 0, Bcap = 0;
   uint32_t *keys, *vals, *keys_alt, *vals_alt, *counts, *start;
-  float4 *edge, *aedge;            // band-edge tables of the node and auxiliary cells
+  float4 *edge = nullptr, *aedge;  // band-edge tables of the node (current B) and auxiliary cells
+  float4* edge_all = nullptr;      // the node tables of every B up to Bcap
   const uint32_t *perm = nullptr, *skeys = nullptr;
   double *px, *py, *pz, *sw, *sy;
   float4* pf;
@@ -186,7 +187,15 @@ void carve(hamls_plan_s* P) {
   P->vals_alt = A.take<uint32_t>(M);
   P->counts = A.take<uint32_t>((size_t)256 * radix_blocks(sortmax) + scan_partials(sortmax));
   P->start = A.take<uint32_t>((size_t)P->Bcap * 2 * P->Bcap + 1);
-  P->edge = A.take<float4>((size_t)P->Bcap + 1);
+  // band-edge tables of every cell structure up to the capacity's (B = 16,
+  // 32, ..., Bcap: B + 1 entries each, built once); a replan selects the one
+  // of its node count, so no replan's work depends on an earlier one's (a
+  // replan captured in a CUDA graph replays the same whatever ran before)
+  {
+    size_t ne = 0;
+    for (int b = 16; b <= P->Bcap; b *= 2) ne += (size_t)b + 1;
+    P->edge_all = A.take<float4>(ne);
+  }
   P->aedge = A.take<float4>((size_t)P->aB + 1);
   P->px = A.take<double>(M);
   P->py = A.take<double>(M);
@@ -327,9 +336,10 @@ hamls_status build_nodes(hamls_plan_s* P, const double* nodes, const double* wts
   // gives the same result in any plan that holds its nodes
   P->B = key_bands(M);
   P->P = 2 * P->B;
-  if (P->edge_B != P->B) {
-    build_edge_table(P->B, P->edge, s, &P->launches);
-    P->edge_B = P->B;
+  {
+    size_t off = 0;
+    for (int b = 16; b < P->B; b *= 2) off += (size_t)b + 1;
+    P->edge = P->edge_all + off;
   }
   P->op_valid = false;   // a refit operator belongs to the nodes it was built for
   P->has_weights = wts != nullptr;
@@ -392,6 +402,13 @@ hamls_status build_static(hamls_plan_s* P, cudaStream_t s) {
   if (!P->tables) return cuda_status(te == cudaSuccess ? cudaErrorMemoryAllocation : te);
   P->g = P->tables->g;
   build_edge_table(P->aB, P->aedge, s, &P->launches);
+  {
+    size_t off = 0;
+    for (int b = 16; b <= P->Bcap; b *= 2) {
+      build_edge_table(b, P->edge_all + off, s, &P->launches);
+      off += (size_t)b + 1;
+    }
+  }
   fibonacci_points(P->ax, P->ay, P->az, P->M_aux, s, &P->launches);
   CellBuild cb;
   memset(&cb, 0, sizeof(cb));

@@ -68,7 +68,10 @@ __global__ void gl_kernel(int N, double* t_out, double* w_out, double* s_out, fl
     legendre_pd(n, u, P, D);
     const double dth = P * sin(th) / (n * (D - u * P));
     th -= dth;
-    if (fabs(dth) <= 1e-17 * th) break;
+    // Newton converges quadratically: after a correction of 1e-14 the
+    // error is far below FP64 resolution (a threshold under the resolution
+    // itself would never be met and run every iteration)
+    if (fabs(dth) <= 1e-14 * th) break;
   }
   sh = sin(0.5 * th);
   u = middle ? 1.0 : 2.0 * sh * sh;

@@ -5,7 +5,8 @@
 * every request of a serving mix (continuous batching over several streams,
   plans reused, fits overlapping on the device) equals the same request
   fitted alone, including an N = 1024 request;
-* a batch captured in one CUDA graph equals its fits run alone;
+* a batch captured in one CUDA graph equals its fits run alone, replayed
+  twice on plans that ran other fits before the capture;
 * a fit with a non-finite value reports its own status in the batch while
   the fits around it (on the same plan) report none.
 """
@@ -111,7 +112,13 @@ def test_batch_equals_alone_and_reports_per_fit_status(h, graph):
             y[5] = float("nan")
         return x, y
     pool = PlanPool(device=torch.device("cuda"), min_capacity=1 << 15)
-    res = run_batch(specs, load, pool, n_slots=3, precision="mixed", device=torch.device("cuda"), graph=graph)
+    if graph:
+        # plans that have run other fits first, then a captured batch replayed
+        # twice: a slot's fits change cell structure from one fit to the next,
+        # and every replay must give the same as the fits alone
+        run_batch(specs[::-1], load, pool, n_slots=3, precision="mixed", device=torch.device("cuda"))
+    res = run_batch(specs, load, pool, n_slots=3, precision="mixed", device=torch.device("cuda"), graph=graph,
+                    replays=2 if graph else 1)
     assert res.graph == graph
     st = np.array(res.status)
     assert st[bad] == 7 and np.all(np.delete(st, bad) == 0)
