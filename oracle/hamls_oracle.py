@@ -65,6 +65,7 @@ class Params:
     aux_radius: float = 3.0    # Shepard radius / sqrt(4 pi / M_aux)
     pivot_floor: float = 1e-12  # Cholesky pivot (squared) below which a direction is dropped
     bisect_iters: int = 200
+    weight_fn: int = 0         # phi of eq. weight_function_radial: 0 Wendland phi_{3,2}, 1 phi_{3,1}
 
     def n_for(self, K: int) -> int:
         return self.n_target if self.n_target > 0 else 4 * dim_tan(K)
@@ -200,6 +201,26 @@ def wendland(r):
     return om ** 6 * (35 * r * r + 18 * r + 3)
 
 
+def wendland31(r):
+    """Wendland function phi_{3,1}(r) = (1-r)^4 (4 r + 1) on [0,1), 0 beyond:
+    continuous, nonincreasing, supp = [0, 1], C^2 as a radial function (the
+    other Wendland choice that Sec. 2.2 leaves open; below the C^3 that
+    Sec. 2.3 names for a C^3 smoothed tau)."""
+    r = np.asarray(r)
+    one = r.dtype.type(1)
+    om = np.where(r < one, one - r, r.dtype.type(0))
+    return om ** 4 * (4 * r + 1)
+
+
+def weight_phi(r, fn: int = 0):
+    """phi of eq. weight_function_radial: 0 -> phi_{3,2}, 1 -> phi_{3,1}."""
+    if fn == 0:
+        return wendland(r)
+    if fn == 1:
+        return wendland31(r)
+    raise ValueError(f"weight_fn {fn}: 0 (phi_3,2) or 1 (phi_3,1)")
+
+
 # --------------------------------------------------------------------------
 # k nearest neighbours and the adaptive support radius (eq. adaptive_support_radius)
 # --------------------------------------------------------------------------
@@ -230,10 +251,10 @@ class NodeSet:
         return np.sort(cand[c2 < rho2])
 
 
-def shepard(q: np.ndarray, aux: np.ndarray, aux_tree: cKDTree, values: np.ndarray, rho: float):
+def shepard(q: np.ndarray, aux: np.ndarray, aux_tree: cKDTree, values: np.ndarray, rho: float, weight_fn: int = 0):
     """Degree-zero MLS (Shepard) of values given at aux points, with constant
-    geodesic support radius rho and the Wendland weight (Sec. 2.2, last
-    paragraph). Extended precision."""
+    geodesic support radius rho and the weight phi of eq.
+    weight_function_radial (Sec. 2.2, last paragraph). Extended precision."""
     rho2 = float(chord_radius2(rho))
     out = np.empty(len(q), dtype=LD)
     cands = aux_tree.query_ball_point(q, math.sqrt(rho2) * (1 + 1e-9))
@@ -242,7 +263,7 @@ def shepard(q: np.ndarray, aux: np.ndarray, aux_tree: cKDTree, values: np.ndarra
         c2 = chord2(q[j][None, :], aux[c])
         c = c[c2 < rho2]
         d = geodesic_from_chord2(chord2(q[j][None, :].astype(LD), aux[c].astype(LD)))
-        wt = wendland(d / LD(rho))
+        wt = weight_phi(d / LD(rho), weight_fn)
         out[j] = np.sum(wt * values[c].astype(LD)) / np.sum(wt)
     return out
 
@@ -278,7 +299,7 @@ def support_radius(nodes: NodeSet, q: np.ndarray, K: int, p: Params, subset=None
     dn_aux = np.full(M_aux, np.nan, dtype=LD)
     if len(need):
         dn_aux[need] = geodesic_from_chord2(nodes.knn_chord2(aux[need], n).astype(LD))
-    dtil = shepard(qs, aux, aux_tree, dn_aux, rho)
+    dtil = shepard(qs, aux, aux_tree, dn_aux, rho, p.weight_fn)
     delta = (1 + LD(p.eps)) * dtil
     rho2 = chord_radius2(delta.astype(np.float64))
     count = np.array([len(nodes.ball(qs[j], rho2[j])) for j in range(len(qs))], dtype=np.int64)
@@ -356,16 +377,16 @@ class LocalResult:
     wn: np.ndarray = field(repr=False, default=None)
 
 
-def local_design(q_ld, xs, delta, vs, K, frame=None):
+def local_design(q_ld, xs, delta, vs, K, frame=None, weight_fn: int = 0):
     """Normalised weights and the scaled design B of eq. (mls local vectors).
 
-    Weights w_i = v_i phi(d_i / delta), normalised to sum 1; basis g_j =
+    Weights w_i = v_i phi(d_i / delta) (phi by weight_fn), normalised to sum 1; basis g_j =
     monomials of the tangent coordinates (u, v) = (e1 . x_i, e2 . x_i) of the
     orthogonal projection onto T_q S^2, centred at q (g_j(q) = 0 for j >= 2),
     each column scaled to unit discrete norm sum_i w_i g_j(x_i)^2 = 1."""
     xs_ld = xs.astype(LD)
     d = geodesic_from_chord2(chord2(q_ld[None, :], xs_ld))
-    w = wendland(d / LD(delta)) * (np.ones(len(xs), dtype=LD) if vs is None else vs.astype(LD))
+    w = weight_phi(d / LD(delta), weight_fn) * (np.ones(len(xs), dtype=LD) if vs is None else vs.astype(LD))
     wn = w / np.sum(w)
     e1, e2 = tangent_frame(q_ld) if frame is None else frame
     u = (xs_ld @ e1) / LD(delta)
@@ -463,7 +484,7 @@ def gauss_solve(A: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 def mls_at(q_ld, xs, ys, delta, K, p: Params, vs=None, frame=None, tau_override=None) -> LocalResult:
     """Regularised MLS value at one centre q from its local nodes."""
-    B, wn, degrees = local_design(q_ld, xs, delta, vs, K, frame)
+    B, wn, degrees = local_design(q_ld, xs, delta, vs, K, frame, p.weight_fn)
     yw = np.sqrt(wn) * ys.astype(LD)
     res = solve_local(B, yw, degrees, p, tau_override)
     res.wn = wn

@@ -51,12 +51,13 @@ def _tangent_poly(q, xs, K, seed):
 Q = np.array([0.36, -0.48, 0.8])
 
 
+@pytest.mark.parametrize("weight_fn", [0, 1])
 @pytest.mark.parametrize("K", [1, 2, 3, 4])
-def test_reproduces_tangent_polynomials_without_regularisation(K):
+def test_reproduces_tangent_polynomials_without_regularisation(K, weight_fn):
     q = Q / np.linalg.norm(Q)
     xs = _cap_nodes(q, 0.2, 4 * O.dim_tan(K), seed=K)
     y, p0 = _tangent_poly(q, xs, K, seed=10 + K)
-    p = O.Params(chi_target=1e300, chi_full=2e300)
+    p = O.Params(chi_target=1e300, chi_full=2e300, weight_fn=weight_fn)
     res = O.mls_at(q.astype(LD), xs, y, LD(0.2), K, p)
     assert res.tau_tilde == 0
     assert abs(float(res.c1) - p0) < 1e-13 * (1 + abs(p0))
@@ -214,6 +215,62 @@ def test_wendland_shape():
         h = 1e-3
         pts = [O.wendland(np.array(1.0 - i * h)) for i in range(k + 1)]
         assert abs(sum((-1) ** i * math.comb(k, i) * pts[i] for i in range(k + 1)) / h ** k) < 1e5 * h ** (6 - k)
+
+
+def _wendland_operator(f, r):
+    """Wendland's integral operator (I f)(r) = int_r^1 t f(t) dt, numerically."""
+    from scipy.integrate import quad
+    return np.array([quad(lambda t: t * f(t), float(x), 1.0, epsabs=1e-15, epsrel=1e-13)[0] for x in np.atleast_1d(r)])
+
+
+def test_wendland_functions_from_their_construction():
+    # phi_{3,k} = I^k (1 - r)_+^(floor(3/2) + k + 1) up to a constant factor
+    # (Wendland's construction of the compactly supported functions that
+    # Sec. 2.2 names): phi_{3,1} from one application to (1 - r)^3, phi_{3,2}
+    # from two applications to (1 - r)^4. Checked on the shape, the constant
+    # factor fitted at one point.
+    r = np.linspace(0.0, 0.95, 12)
+    i1 = _wendland_operator(lambda t: (1 - t) ** 3, r)
+    w31 = O.wendland31(r)
+    assert np.allclose(w31 / w31[0], i1 / i1[0], rtol=1e-10)
+    i2 = _wendland_operator(lambda t: _wendland_operator(lambda s: (1 - s) ** 4, t)[0], r)
+    w32 = O.wendland(r)
+    assert np.allclose(w32 / w32[0], i2 / i2[0], rtol=1e-9)
+    assert np.all(O.wendland31(np.array([1.0, 1.3])) == 0) and np.all(np.diff(O.wendland31(np.linspace(0, 1, 50))) <= 0)
+
+
+def test_wendland_radial_smoothness():
+    # phi(|x|) is C^(2k) for phi_{3,k}: on [0, 1] a polynomial whose odd
+    # derivatives at 0 vanish up to order 2k - 1 but not at order 2k + 1, and
+    # whose derivatives at r = 1 vanish up to order 2k + 1 (flat joint to 0)
+    from numpy.polynomial import Polynomial
+    r = np.linspace(0, 1, 40)
+    for fn, k in ((1, 1), (0, 2)):
+        P = Polynomial.fit(r, O.weight_phi(r, fn), 4 + 2 * k).convert()
+        for d in range(1, 2 * k, 2):
+            assert abs(P.deriv(d)(0.0)) < 1e-6
+        assert abs(P.deriv(2 * k + 1)(0.0)) > 1.0
+        for d in range(0, 2 * k + 2):
+            assert abs(P.deriv(d)(1.0)) < 1e-6 * max(1.0, abs(P.deriv(2 * k + 2)(1.0)))
+    with pytest.raises(ValueError):
+        O.weight_phi(r, 2)
+
+
+def test_weight_fn_reaches_the_local_problem_and_the_shepard_radius():
+    # the same local data under the two weights: equal on polynomials (above),
+    # different on a general function; and the smoothed support radius moves
+    q = Q / np.linalg.norm(Q)
+    xs = _cap_nodes(q, 0.2, 40, seed=4)
+    y = np.exp(3 * xs[:, 0]) * np.cos(5 * xs[:, 2])
+    a = O.mls_at(q.astype(LD), xs, y, LD(0.2), 2, O.Params())
+    b = O.mls_at(q.astype(LD), xs, y, LD(0.2), 2, O.Params(weight_fn=1))
+    assert abs(float(a.c1) - float(b.c1)) > 1e-6
+    x = uniform_sphere(SplitMix64(23), 3000)
+    g = O.quad_grid(8)
+    s0 = O.support_radius(O.NodeSet(x), g.xyz, 2, O.Params())
+    s1 = O.support_radius(O.NodeSet(x), g.xyz, 2, O.Params(weight_fn=1))
+    assert np.array_equal(s0.dn_aux[~np.isnan(s0.dn_aux)], s1.dn_aux[~np.isnan(s1.dn_aux)])
+    assert np.max(np.abs(s0.delta - s1.delta)) > 0
 
 
 def test_knn_brute_force():
