@@ -816,6 +816,22 @@ def run_ours(args):
     if refit is not None:
         refit["roofline"]["peak"] = hbm_peak
         refit["roofline"]["frac"] = refit["roofline"]["achieved"] / hbm_peak
+    # the MLS stage as a whole (auxiliary k-NN, Shepard support radius, work
+    # order, gather + local solves): its stages' bytes over their summed time.
+    # Shepard: about pi aux_radius^2 = 28 auxiliary members per grid node
+    # (column, weight, d_n: 12 B each in the mixed form) + 41 B of per-node
+    # inputs and outputs; work order: a key/value sort of M_Q entries (16 B)
+    shep_nnz = MQ * math.pi * 3.0 ** 2
+    extra = {"shepard": shep_nnz * 12 + MQ * 41, "order": MQ * 16}
+    mls_parts = ("aux_knn", "shepard", "order", "mls")
+    if all(stages.get(k, 0.0) > 0 for k in mls_parts):
+        ms_sum = sum(stages[k] for k in mls_parts)
+        b_sum = alg["aux_knn"][1] + alg["mls"][1] + extra["shepard"] + extra["order"]
+        ach = b_sum / (ms_sum / 1000.0) / 1e9
+        stage_roof["mls_stage"] = {"kernel": "aux_knn_kernel + shepard_apply_kernel + work-order sort + "
+                                   "mls_gather_kernel + mls_solve_kernel + redo_kernel", "ms": round(ms_sum, 4),
+                                   "algorithmic_bytes": int(b_sum), "achieved_gbs": round(ach, 1),
+                                   "frac": round(ach / hbm_peak, 4), "traffic": None}
     dom = max(alg, key=lambda k: stages.get(k, 0.0))      # the slowest stage with a byte count
     dr = stage_roof.get(dom)
     roof = {"bound": "hbm", "kernel": dr["kernel"] if dr else dom, "achieved": dr["achieved_gbs"] if dr else None,

@@ -78,6 +78,11 @@ typedef struct {
   int     precision;    /* hamls_precision; default HAMLS_FP64 */
   double  fp64_pivot;   /* MIXED only: squared FP32 pivot below which the local Cholesky is
                            redone in FP64; default 1e-4 */
+  int     weight_fn;    /* phi of eq. weight_function_radial, for the MLS weights and the Shepard
+                           weights of the support radius (Sec. 2.2 leaves the Wendland function
+                           open): 0 = phi_{3,2}(r) = (1-r)^6 (35 r^2 + 18 r + 3), C^4 (default);
+                           1 = phi_{3,1}(r) = (1-r)^4 (4 r + 1), C^2 (then the smoothed tau of
+                           Sec. 2.3 is C^2, not C^3). Other values: HAMLS_ERR_INVALID_ARG */
 } hamls_params;
 
 /* Per-plan statistics of the last plan/replan and fit. */

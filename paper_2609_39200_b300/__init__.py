@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
     _fields_ = [("n_target", ctypes.c_int), ("eps", ctypes.c_double), ("chi_target", ctypes.c_double),
                 ("chi_full", ctypes.c_double), ("sobolev_s", ctypes.c_double), ("aux_points", ctypes.c_int64),
                 ("aux_radius", ctypes.c_double), ("pivot_floor", ctypes.c_double), ("precision", ctypes.c_int),
-                ("fp64_pivot", ctypes.c_double)]
+                ("fp64_pivot", ctypes.c_double), ("weight_fn", ctypes.c_int)]
 
 
 class FitStats(ctypes.Structure):

@@ -297,6 +297,7 @@ SupportArgs support_args(hamls_plan_s* P) {
   a.m = P->m;
   a.N = P->N;
   a.eps = P->p.eps;
+  a.weight_fn = P->p.weight_fn;
   a.rho_aux = P->p.aux_radius * sqrt(4.0 * M_PI / (double)P->M_aux);
   a.ring_t = P->g.t;
   a.ring_s = P->g.s;
@@ -463,6 +464,7 @@ bool validate_params(const hamls_params& p) {
   if (!(p.aux_radius > 0) || p.aux_points < 0 || !(p.pivot_floor >= 0) || !(p.fp64_pivot >= 0)) return false;
   if (p.precision != HAMLS_FP64 && p.precision != HAMLS_MIXED) return false;
   if (p.n_target < 0 || p.n_target > KNN_MAX) return false;
+  if (p.weight_fn != 0 && p.weight_fn != 1) return false;
   return true;
 }
 
@@ -492,6 +494,7 @@ void hamls_default_params(hamls_params* p) {
   p->pivot_floor = 1e-12;
   p->precision = HAMLS_FP64;
   p->fp64_pivot = 1e-4;
+  p->weight_fn = 0;
 }
 
 const char* hamls_status_string(hamls_status s) {
@@ -691,6 +694,7 @@ static MlsArgs mls_args(hamls_plan_s* P) {
   a.chiF = P->p.chi_full;
   a.floor_ = P->p.pivot_floor;
   a.fp64_pivot = P->p.fp64_pivot;
+  a.weight_fn = P->p.weight_fn;
   for (int l = 0; l <= KMAX; ++l) a.mu[l] = pow((double)l * (l + 1), P->p.sobolev_s);
   a.mom = P->mom;
   a.redo_list = P->redo_list;

@@ -403,6 +403,20 @@ __device__ __forceinline__ T wendland(T r) {
   return om6 * ((T(35) * r + T(18)) * r + T(3));
 }
 
+// Wendland phi_{3,1}(r) = (1-r)^4 (4 r + 1) on [0,1).
+template <typename T>
+__device__ __forceinline__ T wendland31(T r) {
+  T om = r < T(1) ? T(1) - r : T(0);
+  T om2 = om * om;
+  return om2 * om2 * (T(4) * r + T(1));
+}
+
+// phi of eq. weight_function_radial: fn 0 -> phi_{3,2} (default), 1 -> phi_{3,1}
+template <typename T>
+__device__ __forceinline__ T weight_phi(int fn, T r) {
+  return fn == 1 ? wendland31(r) : wendland(r);
+}
+
 __device__ __forceinline__ double geodesic_from_chord2(double c2) { return 2.0 * asin(0.5 * sqrt(c2)); }
 __device__ __forceinline__ float geodesic_from_chord2(float c2) { return 2.f * asinf(0.5f * sqrtf(c2)); }
 

@@ -111,6 +111,7 @@ struct SupportArgs {
   Cells nodes;                  // scattered nodes
   Cells aux;                    // auxiliary grid
   int n_target, m, N;
+  int weight_fn;                // phi: 0 Wendland phi_{3,2}, 1 phi_{3,1}
   double eps, rho_aux;
   const double *ring_t, *ring_s, *cphi, *sphi;
   double* dn_aux_sorted;        // aux d_n (geodesic), sorted aux order
@@ -170,6 +171,7 @@ struct MlsArgs {
   double* chi;
   double* tau;
   double chiT, chiF, floor_, fp64_pivot;
+  int weight_fn;                // phi: 0 Wendland phi_{3,2}, 1 phi_{3,1}
   double mu[KMAX + 1];
   void* mom;                    // per work-order position: moments (float MIXED, double FP64)
   uint32_t* redo_list;          // MIXED: work-order positions re-solved in FP64

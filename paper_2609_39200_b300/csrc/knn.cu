@@ -508,11 +508,11 @@ __global__ void __launch_bounds__(128) shepard_rows_kernel(SupportArgs a, double
           if (c2f <= hi_f) {
             const double c2 = chord2_exact(a.aux.px[idx], a.aux.py[idx], a.aux.pz[idx], qx, qy, qz);
             in = c2 < rho_aux2;
-            if (in && FILL) w = wendland(geodesic_from_chord2(c2) / a.rho_aux);
+            if (in && FILL) w = weight_phi(a.weight_fn, geodesic_from_chord2(c2) / a.rho_aux);
           }
         } else {
           in = c2f < r2_f;
-          if (in && FILL) wf = wendland(geodesic_from_chord2(c2f) * irho_f);
+          if (in && FILL) wf = weight_phi(a.weight_fn, geodesic_from_chord2(c2f) * irho_f);
         }
       }
       const unsigned b = __ballot_sync(FULL, in);

@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(MLS_WARPS * 32, 7) mls_gather_kernel(MlsArgs a
           const float c2 = dx * dx + dy * dy + dz * dz;
           if (!(c2 < r2f)) return;
           ++nin;
-          float w = wendland(geodesic_from_chord2(c2) * idf);
+          float w = weight_phi(a.weight_fn, geodesic_from_chord2(c2) * idf);
           if (a.swf) w *= a.swf[idx];
           const float u = e1x * dx + e1y * dy + e1z * dz;
           const float v = e2x * dx + e2y * dy;
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(MLS_WARPS * 32, 7) mls_gather_kernel(MlsArgs a
           if (!(c2 < rho2)) return;
           ++nin;
           const double dx = X - qx, dy = Y - qy, dz = Z - qz;
-          double w = wendland(geodesic_from_chord2(c2) * id);
+          double w = weight_phi(a.weight_fn, geodesic_from_chord2(c2) * id);
           if (a.sw) w *= a.sw[idx];
           const double u = e1x * dx + e1y * dy + e1z * dz;
           const double v = e2x * dx + e2y * dy;
@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(128) op_rows_kernel(MlsArgs a, const double* _
           const float c2 = dx * dx + dy * dy + dz * dz;
           in = c2 < r2f;
           if (in && FILL) {
-            w = wendland(geodesic_from_chord2(c2) * idf);
+            w = weight_phi(a.weight_fn, geodesic_from_chord2(c2) * idf);
             if (a.swf) w *= a.swf[idx];
             u = e1x * dx + e1y * dy + e1z * dz;
             v = e2x * dx + e2y * dy;
@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(128) op_rows_kernel(MlsArgs a, const double* _
             in = c2 < rho2;
             if (in && FILL) {
               const double dx = X - qx, dy = Y - qy, dz = Z - qz;
-              w = wendland(geodesic_from_chord2(c2) * id);
+              w = weight_phi(a.weight_fn, geodesic_from_chord2(c2) * id);
               if (a.sw) w *= a.sw[idx];
               u = e1x * dx + e1y * dy + e1z * dz;
               v = e2x * dx + e2y * dy;

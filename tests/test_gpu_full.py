@@ -5,8 +5,10 @@
   against the known truth.
 * N=512, K=3, M=4M (the benchmark's workload and launch configuration): the
   oracle evaluates a seeded sample of grid nodes one by one; the GPU's MLS
-  values there must match, and the mixed form's error against the truth must
-  stay within 1.05x of the FP64 form's."""
+  values there must match (FP64 to 1e-9; mixed within a bound set by each
+  node's own local problem: its n, chi and the condition of its Gram
+  matrix), and the mixed form's error against the truth must stay within
+  1.05x of the FP64 form's."""
 import numpy as np
 import pytest
 import torch
@@ -100,18 +102,38 @@ def test_n512_sampled_grid_values_and_error_bar(h, cfg3):
     scale = np.max(np.abs(g64["f"]))
     assert np.max(np.abs(g64["f"][sample] - fo)) < 1e-9 * scale
     assert np.array_equal(g64["count"][sample], sup.count)
-    # MIXED: FP32 moments and solves. Well-posed local problems agree to a few
-    # FP32 roundings; the sample also holds the most ill-conditioned nodes of
-    # the grid, whose FP32 solves (condition up to ~1/fp64_pivot = 1e4 before
-    # the FP64 re-solve takes over) may move by up to 1e4 * 2^-24 * local
-    # amplification. The binding criterion is the L2 error bar below.
+    # MIXED: FP32 moments and solves, per node within a bound set by that
+    # node's own local problem (Sec. 2.3, the closed form of c_1): the FP32
+    # moments perturb the normalised Gram matrix H = B^T B by about n u
+    # (u = 2^-24; each entry a weighted sum of n terms of size <= 1), the
+    # Cholesky of its tangent block C = L L^T amplifies that by cond(C), and
+    # c_1 by chi = 1 / (1 - |L^-1 b|^2) (eq. chi via coupling), all in units
+    # of the largest local value |y_i|:
+    #     |f_mixed - f| <= 16 u (sqrt(n) + m) chi cond(C) max_i |y_i|.
+    # chi, cond(C), n and the local values come from the oracle's own local
+    # problem at each sampled node (FP64 re-solves, taken where an FP32 pivot
+    # falls below fp64_pivot, land far inside).
     gm = res["mixed"][1]
-    err = np.abs(gm["f"][sample] - fo) / scale
-    worst = sample[np.argmax(err)]
-    info = (float(err.max()), int(worst), float(g64["chi"][worst]), int(g64["count"][worst]))
-    assert np.median(err) < 1e-5, info
-    assert np.percentile(err, 90) < 1e-4, info
-    assert err.max() < 1e-2, info
+    nodes = O.NodeSet(w.nodes)
+    m = O.dim_tan(w.K)
+    tol = np.empty(len(sample))
+    for jj, j in enumerate(sample):
+        idx = nodes.ball(grid.xyz[j], sup.rho2[jj])
+        loc = O.mls_at(grid.xyz_ld[j], w.nodes[idx], w.values[idx], sup.delta[jj], w.K, O.Params())
+        Lf = np.asarray(loc.L, dtype=np.float64)
+        Cj = Lf @ Lf.T
+        keep = np.diag(Cj) > 0
+        kappa = float(np.linalg.cond(Cj[np.ix_(keep, keep)])) if keep.any() else 1.0
+        chi_j = float(min(loc.chi, O.LD(1e30)))
+        tol[jj] = 16 * 2.0 ** -24 * (np.sqrt(loc.n) + m) * max(chi_j, 1.0) * kappa * np.max(np.abs(w.values[idx]))
+    err = np.abs(gm["f"][sample] - fo)
+    ratio = err / tol
+    worst = sample[np.argmax(ratio)]
+    info = (float(ratio.max()), int(worst), float(g64["chi"][worst]), int(g64["count"][worst]),
+            float(np.median(err / scale)), float(np.max(err / scale)))
+    assert np.all(err <= tol), info
+    # and most nodes agree to a few FP32 roundings of the grid's largest value
+    assert np.median(err / scale) < 1e-5, info
     e64 = truth_error(res["fp64"][0], w.truth, w.N)
     emx = truth_error(res["mixed"][0], w.truth, w.N)
     assert emx <= 1.05 * e64, (emx, e64)
