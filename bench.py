@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--clocks-csv", default=None, help="also write the clock samples here ({rank} = the rank)")
     ap.add_argument("--quick", action="store_true", help="skip the FP64 form, e2e and CPU baseline (profiling)")
     ap.add_argument("--cache", default=None, help="directory to keep/reuse the generated workload (profiling runs)")
+    ap.add_argument("--nodes", type=int, default=None, help="profiling runs: the benchmark workload generated with "
+                    "this many nodes instead of its 4M (the line's config names the smaller workload)")
     ap.add_argument("--fp64-pivot", type=float, default=None, help="mixed form: squared FP32 pivot below which a "
                     "local solve is redone in FP64 (library default if omitted)")
     ap.add_argument("--batch-sets", type=int, default=64, help="value sets of the many-sets leg (0: skip)")
@@ -346,16 +348,27 @@ class Clocks:
 
 
 # --------------------------------------------------------------------- ours
-def load_workload(cache, rank, torch, dev):
-    """The seeded benchmark workload; with a cache directory, generated once and reused."""
+def workload_name(nodes):
+    """The benchmark workload's name, or that of its reduced form (--nodes)."""
+    if not nodes:
+        return WORKLOAD
+    tag = f"m{nodes // 1_000_000}m" if nodes % 1_000_000 == 0 else f"m{nodes // 1000}k"
+    return WORKLOAD.rsplit("_", 1)[0] + "_" + tag
+
+
+def load_workload(cache, rank, torch, dev, nodes=None):
+    """The seeded benchmark workload (with nodes: generated with that many
+    nodes, for profiling runs); with a cache directory, generated once and
+    reused."""
     from hamls_synth import workload
     from hamls_synth.gen import Workload
 
-    path = os.path.join(cache, f"{WORKLOAD}_{rank}.npz") if cache else None
+    name = workload_name(nodes)
+    path = os.path.join(cache, f"{name}_{rank}.npz") if cache else None
     if path and os.path.exists(path):
         z = np.load(path, allow_pickle=False)
-        return Workload(WORKLOAD, int(z["N"]), int(z["K"]), int(z["M"]), z["nodes"], z["values"], z["truth"], {})
-    w = workload(WORKLOAD, fit_index=rank, xp=torch, device=dev)
+        return Workload(name, int(z["N"]), int(z["K"]), int(z["M"]), z["nodes"], z["values"], z["truth"], {})
+    w = workload(WORKLOAD, fit_index=rank, xp=torch, device=dev, M=nodes)
     if path:
         os.makedirs(cache, exist_ok=True)
         np.savez(path, N=w.N, K=w.K, M=w.M, nodes=w.nodes, values=w.values, truth=w.truth)
@@ -539,7 +552,7 @@ def run_ours(args):
     h.lib()
 
     # CPU baseline first (rank 0, N=1), before any GPU work
-    w = load_workload(args.cache, rank, torch, dev)
+    w = load_workload(args.cache, rank, torch, dev, args.nodes)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         try:
@@ -844,7 +857,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "fits/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "N": w.N, "K": w.K, "M": w.M, "grid_nodes": MQ,
+                "config": {"workload": workload_name(args.nodes), "N": w.N, "K": w.K, "M": w.M, "grid_nodes": MQ,
                            "precision": "mixed", "parallelism": f"replicas x{world}" if world > 1 else "single",
                            "l2": "256 MiB write between timed steps"},
                 "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},

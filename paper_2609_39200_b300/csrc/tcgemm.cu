@@ -12,15 +12,17 @@
 // matrix (degrees x latitudes).
 //
 // One CTA (4 warps) computes a 128 x NT tile of D (NT <= 256 columns of
-// tensor memory). Per K step of 32 (one 128-byte row of a swizzled tile):
-// TMA brings the A and B tiles (boxes of 32 rows x 32 FP32, 128-byte
-// swizzle) into one of two shared-memory stages, all threads split them into
-// hi (in place) and lo tiles, and one thread issues the 4 x 3 tcgen05.mma of
-// the step; tcgen05.commit frees the stage for the TMA two steps ahead. The
+// tensor memory). The hi and lo parts of both operands are split once, when
+// they are written (the quadrature matrix at table build, the spectra by
+// fold_spectra_kernel), and held in global memory. Per K step of 32 (one
+// 128-byte row of a swizzled tile) one thread has TMA bring the four tiles
+// (A hi, A lo, B hi, B lo; boxes of 32 rows x 32 FP32, 128-byte swizzle) into
+// one of two shared-memory stages and issues the 4 x 3 tcgen05.mma of the
+// step; tcgen05.commit frees the stage for the TMA two steps ahead. The
 // epilogue reads D from tensor memory (warp w owns lanes 32w..32w+31) and
 // hands 16 columns at a time to the caller's epilogue.
 //
-// Every wait on an mbarrier is bounded (about a second of clock); a wait
+// Every wait on an mbarrier is bounded (about two seconds of clock); a wait
 // that gives up sets an error flag, the CTA skips its remaining work, waits
 // (bounded again) for the copies and products it has in flight, frees its
 // tensor memory and returns.
@@ -33,6 +35,7 @@
 #include "../../include/hamls_debug.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "mbarrier.cuh"
 
 namespace hamls {
 
@@ -44,39 +47,8 @@ constexpr int TC_TILE_A = 128 * TC_BK * 4;              // 16 KB
 constexpr int TC_TILE_B = TC_MAXN * TC_BK * 4;          // 32 KB
 constexpr int TC_STAGE = 2 * TC_TILE_A + 2 * TC_TILE_B; // hi and lo of both: 96 KB
 constexpr int TC_SMEM = 2 * TC_STAGE + 1024 + 256;      // two stages, alignment, barriers
-constexpr long long TC_WAIT_CYCLES = 4000000000ll;      // about 2 s at 2 GHz
 
 // ------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait for the phase with the given parity to complete
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
-  }
-  return true;
-}
-
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
@@ -218,7 +190,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     for (int kt = 0; kt < KT && ok; ++kt) {
       const int s = kt & 1;
       const uint32_t ph = (uint32_t)(kt >> 1) & 1u;
-      if (!mbar_wait(&full[s], ph)) {
+      if (!mbar_wait_bounded(&full[s], ph)) {
         ok = false;
         break;
       }
@@ -237,7 +209,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       mma_commit(&empty[s]);
       if (kt + 2 < KT) {
         // the stage is free once these products have read it
-        if (!mbar_wait(&empty[s], ph)) {
+        if (!mbar_wait_bounded(&empty[s], ph)) {
           ok = false;
           break;
         }
@@ -251,11 +223,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       *bad = 1;
       // wait (bounded) for every stage still loading before the CTA may exit
       for (int s = 0; s < 2; ++s)
-        if (loads[s] > 0) (void)mbar_wait(&full[s], (uint32_t)(loads[s] - 1) & 1u);
+        if (loads[s] > 0) (void)mbar_wait_bounded(&full[s], (uint32_t)(loads[s] - 1) & 1u);
     }
   }
   if (warp == 0) __syncwarp();
-  if (!mbar_wait(done, 0)) atomicExch(bad, 1);
+  if (!mbar_wait_bounded(done, 0)) atomicExch(bad, 1);
   tc_fence_after();
   __syncthreads();
   const bool ok = *bad == 0;
