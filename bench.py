@@ -103,12 +103,12 @@ class OracleBaseline:
         self.t_quad = time.perf_counter() - t0
         self.sup = O.support_radius(self.nodes, self.grid.xyz, w.K, self.p, subset=self.sel)
 
-    def estimate_all_cores(self, frac=0.01) -> dict:
+    def estimate_all_cores(self, frac=0.01, pool=None) -> dict:
         """The same estimate with the per-node work on all host cores: a
         seeded sample of frac of the grid nodes with twice as many auxiliary
         points (a fit has 2 M_Q of them per M_Q grid nodes), so the sample's
         parallel wall time scales to the whole fit by M_Q / sample."""
-        r = oracle_all_cores(self.w, frac)
+        r = oracle_all_cores(self.w, frac, pool=pool)
         per_fit = self.t_build + self.t_aux + r["wall_s"] * self.MQ / r["grid_nodes"] + self.t_quad
         one = self.estimate()
         return {"value": 1.0 / per_fit, "unit": "fits/s", "cores": r["cores"], "kind": "oracle",
@@ -179,31 +179,54 @@ def _oracle_worker_task(sel, asel, barrier):
     return t0, time.time()
 
 
-def oracle_all_cores(w, frac=0.01, seed=11, workers=None):
-    """The oracle's per-node work (d_n at auxiliary points, the Shepard
-    smoothing, ball and local problem at grid nodes) on a seeded sample of
-    frac of the grid nodes and as many auxiliary points, split over all host
-    cores (spawned processes), wall-clock timed from a common start; the
-    once-per-fit parts (trees, grids, the quadrature) as in OracleBaseline."""
-    import multiprocessing as mp
-    from concurrent.futures import ProcessPoolExecutor
+class AllCoresPool:
+    """Spawned worker processes, one per host core, each holding the oracle's
+    node tree and grids for one workload; reused for every timed sample."""
 
-    from hamls_synth import SplitMix64
+    def __init__(self, w, workers=None):
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
 
-    cores = workers or len(os.sched_getaffinity(0))
-    MQ = (w.N + 1) * (2 * w.N + 2)
-    n_sel = max(cores, int(frac * MQ))
-    sel = np.unique((SplitMix64(seed).uniform(n_sel) * MQ).astype(np.int64))
-    asel = np.unique((SplitMix64(seed + 1).uniform(2 * len(sel)) * 2 * MQ).astype(np.int64))
-    ctx = mp.get_context("spawn")
-    with ctx.Manager() as man:
-        barrier = man.Barrier(cores)
-        with ProcessPoolExecutor(max_workers=cores, mp_context=ctx, initializer=_oracle_worker_init,
-                                 initargs=(w.nodes, w.values, w.N, w.K)) as ex:
-            futs = [ex.submit(_oracle_worker_task, sel[i::cores], asel[i::cores], barrier) for i in range(cores)]
-            stamps = [f.result() for f in futs]
-    wall = max(t1 for _, t1 in stamps) - min(t0 for t0, _ in stamps)
-    return {"cores": cores, "grid_nodes": len(sel), "aux_points": len(asel), "wall_s": wall}
+        self.w = w
+        self.cores = workers or len(os.sched_getaffinity(0))
+        ctx = mp.get_context("spawn")
+        self.man = ctx.Manager()
+        self.barrier = self.man.Barrier(self.cores)
+        self.ex = ProcessPoolExecutor(max_workers=self.cores, mp_context=ctx, initializer=_oracle_worker_init,
+                                      initargs=(w.nodes, w.values, w.N, w.K))
+
+    def run(self, frac=0.01, seed=11):
+        """The oracle's per-node work (d_n at auxiliary points, the Shepard
+        smoothing, ball and local problem at grid nodes) on a seeded sample of
+        frac of the grid nodes and twice as many auxiliary points, split over
+        the workers, wall-clock timed from a common start."""
+        from hamls_synth import SplitMix64
+
+        w, cores = self.w, self.cores
+        MQ = (w.N + 1) * (2 * w.N + 2)
+        n_sel = max(cores, int(frac * MQ))
+        sel = np.unique((SplitMix64(seed).uniform(n_sel) * MQ).astype(np.int64))
+        asel = np.unique((SplitMix64(seed + 1).uniform(2 * len(sel)) * 2 * MQ).astype(np.int64))
+        futs = [self.ex.submit(_oracle_worker_task, sel[i::cores], asel[i::cores], self.barrier)
+                for i in range(cores)]
+        stamps = [f.result() for f in futs]
+        wall = max(t1 for _, t1 in stamps) - min(t0 for t0, _ in stamps)
+        return {"cores": cores, "grid_nodes": len(sel), "aux_points": len(asel), "wall_s": wall}
+
+    def close(self):
+        self.ex.shutdown()
+        self.man.shutdown()
+
+
+def oracle_all_cores(w, frac=0.01, seed=11, workers=None, pool=None):
+    """AllCoresPool.run on a given pool, or on a pool made for this call."""
+    if pool is not None:
+        return pool.run(frac, seed)
+    pool = AllCoresPool(w, workers)
+    try:
+        return pool.run(frac, seed)
+    finally:
+        pool.close()
 
 
 def run_reference(args):
@@ -218,9 +241,13 @@ def run_reference(args):
     # of the timed oracle; on the GPU it takes seconds instead of minutes
     w = workload(WORKLOAD, xp=torch, device="cuda" if torch.cuda.is_available() else None)
     ob = OracleBaseline(w, max(8, args.cpu_sample // 4))
-    # each step: the per-node work of a 0.2 % sample on all host cores (the
-    # whole run stays within a few minutes)
-    steps = [ob.estimate_all_cores(0.002) for _ in range(args.warmup + args.steps)]
+    # each step: the per-node work of the main line's sample (args.cpu_frac of
+    # the grid nodes) on all host cores, the workers spawned once
+    pool = AllCoresPool(w)
+    try:
+        steps = [ob.estimate_all_cores(args.cpu_frac, pool=pool) for _ in range(args.warmup + args.steps)]
+    finally:
+        pool.close()
     timed = steps[args.warmup:]
     v = float(np.mean([s["value"] for s in timed]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "fits/s", "n_gpus": args.gpus,
@@ -701,6 +728,45 @@ def run_ours(args):
     if not args.quick:
         voronoi = {"mixed": voronoi_leg(plan, 10)}
 
+    # ---- the forward transform F (hamls_forward) of the fit's coefficients at
+    # the 4M nodes: CUDA events, L2 flushed between calls. FP32 ALU-bound: per
+    # node the (N+1)(N+2)/2 recurrence terms of about 9 FP32 flops each (the
+    # three-term step, the scale, two FMAs into the order's sum); peak = 148 SMs
+    # x 128 FP32 lanes x 2 flops x the SM clock seen during the run.
+    def forward_leg(pl, coeffs, reps):
+        try:
+            pl.set_timing(False)
+            vals = torch.empty(w.M, dtype=torch.float64, device=dev)
+            for _ in range(2):
+                pl.forward(coeffs, out=vals)
+            pl.sync(600000)
+            ts = []
+            for i in range(reps):
+                flush.fill_(float(i))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pl.forward(coeffs, out=vals)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            pl.sync(600000)
+            ms = float(np.mean(ts))
+            terms = (w.N + 1) * (w.N + 2) // 2
+            flops = 9.0 * terms * w.M
+            res = vals.cpu().numpy() - (w.values if isinstance(w.values, np.ndarray) else w.values.cpu().numpy())
+            return {"ms": ms, "points_per_s": w.M / (ms / 1000.0), "reps": reps,
+                    "kernel": "forward_kernel<float> (+ coefficient and factor conversion)",
+                    "roofline": {"bound": "alu", "achieved": flops / (ms / 1000.0) / 1e12, "unit": "TFLOP/s",
+                                 "flops_per_point": 9.0 * terms, "peak_note": "148 SMs x 128 FP32 lanes x 2 x SM clock"},
+                    "residual_rms_over_data_rms": float(np.sqrt(np.mean(res ** 2)) /
+                                                        np.sqrt(np.mean(np.asarray(w.values) ** 2)))}
+        except Exception as e:                  # reported, never fatal to the headline line
+            return {"error": f"{type(e).__name__}: {e}"}
+
+    forward = None
+    if not args.quick:
+        forward = {"mixed": forward_leg(plan, out, 5)}
+
     # ---- e2e: host buffers through the C ABI, copies inside the timed region.
     # Two plans on two streams take the steps in turn, as a caller with a
     # stream of fits would: one step's host-to-device copy overlaps the other
@@ -865,7 +931,7 @@ def run_ours(args):
                 "stage_ms": {k: round(v, 4) for k, v in stages.items()},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk.summary(), "fp64_form": fp64, "refit": refit, "many_sets": many,
-                "batched": batched, "serving": serving, "voronoi": voronoi, "l2_error": l2,
+                "batched": batched, "serving": serving, "voronoi": voronoi, "forward": forward, "l2_error": l2,
                 "mls_stats": {k: stats[k] for k in ("sum_n", "min_n", "max_n", "n_regularized", "n_guarded",
                                                     "n_fp64_redo", "n_dropped")},
                 "knn_stats": {k: stats[k] for k in stats if k.startswith("knn_") or k == "aux_points"}}

@@ -175,6 +175,29 @@ hamls_status hamls_replan(hamls_plan_t plan, const double* nodes_xyz, const doub
 hamls_status hamls_fit(hamls_plan_t plan, const double* values, double* coeffs, cudaStream_t stream);
 
 /*
+ * hamls_forward - the forward transform of the problem statement (Sec. 1, the
+ * sampling matrix F of eq. LSQR-Problem_Regularized): the values
+ *   f(x) = sum_l fhat_l^0 Pbar_l^0(cos theta) + 2 Re sum_{m>=1} e^{i m phi} sum_{l>=m} fhat_l^m Pbar_l^m(cos theta)
+ * of the real field with the plan's bandwidth N whose coefficients are
+ * given in hamls_fit's packing (fully normalised, Condon-Shortley phase), at
+ * points x. With F applied to a fit's coefficients at the plan's nodes, the
+ * values minus the data are the fit's residual.
+ *   coeffs    (N+1)(N+2)/2 complex = 2 (N+1)(N+2)/2 doubles (host or device)
+ *   points    n_points x 3 doubles (device), unit vectors; or NULL for the
+ *             plan's nodes (then n_points must equal their count M, and the
+ *             values come in the node order of the last hamls_plan/hamls_replan)
+ *   values    n_points doubles (device; host allowed with points == NULL)
+ * FP64 plans evaluate in FP64; MIXED plans run the degree recurrence in FP32
+ * with a carried binary exponent (the per-order seed and e^{i m phi} in FP64):
+ * about 1e-6 of the field's scale. Allocates nothing (the plan holds the
+ * workspace). HAMLS_ERR_INVALID_ARG for NULL coeffs/values, a host points or
+ * values array with explicit points, a mismatched n_points, or a reserved
+ * plan without nodes when points == NULL.
+ */
+hamls_status hamls_forward(hamls_plan_t plan, const double* coeffs, const double* points, int64_t n_points,
+                           double* values, cudaStream_t stream);
+
+/*
  * hamls_quadrature_batch - Algorithm 1 step 3 for B sets of grid values at
  * once (eq. quadrature_based_approximation): for value sets that share the
  * bandwidth N (refits of many value series, or fits of different plans of

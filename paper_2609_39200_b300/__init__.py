@@ -63,6 +63,7 @@ _SIGS = {
     "hamls_plan_reserve": (_I, [ctypes.POINTER(_P), _I64, _I, _I, ctypes.POINTER(Params), _P]),
     "hamls_plan_footprint": (_I, [_I64, _I, _I, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]),
     "hamls_fit": (_I, [_P, _P, _P, _P]),
+    "hamls_forward": (_I, [_P, _P, _P, _I64, _P, _P]),
     "hamls_quadrature_batch": (_I, [_P, _P, _P, _I, _P]),
     "hamls_refit_prepare": (_I, [_P, _P]),
     "hamls_refit": (_I, [_P, _P, _P, _P]),
@@ -186,6 +187,24 @@ class Plan:
             out = torch.empty((n_coeffs(self.N), 2), dtype=torch.float64, device=dev)
         self._keep_fit = (values, out)
         _check(lib().hamls_fit(self.h, _ptr(values), _ptr(out), _stream(stream)), "hamls_fit")
+        return out
+
+    def forward(self, coeffs, points=None, out=None, stream=None):
+        """The forward transform (hamls_forward): values of the real field
+        with these coefficients ((ncoef, 2) float64) at the plan's nodes
+        (points=None; node order of the last plan/replan) or at points
+        ((P, 3) float64 device tensor); float64 tensor of the values."""
+        if points is None:
+            n = self.M
+            if out is None:
+                out = torch.empty(n, dtype=torch.float64, device="cuda")
+        else:
+            n = int(points.shape[0])
+            if out is None:
+                out = torch.empty(n, dtype=torch.float64, device=points.device)
+        self._keep_fwd = (coeffs, points, out)
+        _check(lib().hamls_forward(self.h, _ptr(coeffs), _ptr(points), n, _ptr(out), _stream(stream)),
+               "hamls_forward")
         return out
 
     def quadrature_batch(self, fgrid, out=None, stream=None):

@@ -143,6 +143,7 @@ struct hamls_plan_s {
   const uint32_t* order = nullptr;
   void* mom;
   void* F;
+  double2* fwd_ws = nullptr;       // hamls_forward: coefficients and recurrence factors in the plan's precision
   double* coeffs;
   // staging of host inputs
   double *in_nodes, *in_wts, *in_vals;
@@ -242,6 +243,7 @@ void carve(hamls_plan_s* P) {
   P->ovals_alt = A.take<uint32_t>(MQ);
   P->mom = A.take<double>((size_t)MQ * mls_moment_slots(P->K) / (P->mixed ? 2 : 1) + 2);
   P->F = A.take<double2>((size_t)(N + 1) * (N + 1));
+  P->fwd_ws = A.take<double2>(2 * ncoef);
   P->coeffs = A.take<double>(2 * ncoef);
   P->in_nodes = A.take<double>((size_t)3 * M);
   P->in_wts = A.take<double>(M);
@@ -757,6 +759,55 @@ hamls_status hamls_fit(hamls_plan_t P, const double* values, double* coeffs, cud
   stage_end(P, 4, s);
   run_step2(P, s);
   return run_step3(P, coeffs, s);
+}
+
+hamls_status hamls_forward(hamls_plan_t P, const double* coeffs, const double* points, int64_t n_points,
+                           double* values, cudaStream_t s) {
+  if (!P || !coeffs || !values) return HAMLS_ERR_INVALID_ARG;
+  const size_t ncoef = (size_t)(P->N + 1) * (P->N + 2) / 2;
+  ForwardArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = P->N;
+  a.mixed = P->mixed;
+  a.a_rec = P->g.a_rec;
+  a.b_rec = P->g.b_rec;
+  a.cws = P->fwd_ws;
+  a.abws = P->fwd_ws + ncoef;
+  a.num_sms = P->num_sms;
+  double* dv = values;
+  if (points) {
+    // arbitrary points: device arrays only (no staging of a caller-sized set)
+    if (n_points < 0 || !is_device_ptr(points) || !is_device_ptr(values)) return HAMLS_ERR_INVALID_ARG;
+    if (n_points == 0) return HAMLS_OK;
+    a.px = points;
+    a.py = points + 1;
+    a.pz = points + 2;
+    a.stride = 3;
+    a.P = n_points;
+  } else {
+    // the plan's nodes, in sorted order (neighbours share a warp), written
+    // back in the caller's order
+    if (P->M <= 0 || n_points != P->M) return HAMLS_ERR_INVALID_ARG;
+    a.px = P->px;
+    a.py = P->py;
+    a.pz = P->pz;
+    a.stride = 1;
+    a.P = P->M;
+    a.perm = P->perm;
+    if (!is_device_ptr(values)) dv = P->in_vals;
+  }
+  const double* dc = coeffs;
+  if (!is_device_ptr(coeffs)) {
+    HAMLS_TRY(cudaMemcpyAsync(P->coeffs, coeffs, 2 * ncoef * sizeof(double), cudaMemcpyHostToDevice, s));
+    dc = P->coeffs;
+  }
+  a.coeffs = dc;
+  a.out = dv;
+  run_forward(a, s, &P->launches);
+  if (dv != values)
+    HAMLS_TRY(cudaMemcpyAsync(values, dv, (size_t)P->M * sizeof(double), cudaMemcpyDeviceToHost, s));
+  P->last = s;
+  return cuda_status(cudaGetLastError());
 }
 
 hamls_status hamls_refit_prepare(hamls_plan_t P, cudaStream_t s) {

@@ -226,6 +226,27 @@ void run_quadrature(const QuadArgs& a, bool mixed, cudaStream_t s, int64_t* laun
 cudaError_t run_spectra_batch(const GridTables& g, const int* radices, int nrad, const double* fgrid, int B,
                               float2* F, float* Ghi, float* Glo, cudaStream_t s, int64_t* launches);
 
+// ---------------------------------------------------------------- forward.cu
+// The forward transform f(x) = (F fhat)(x) at P points (Sec. 1): coeffs
+// packed complex (device, 2 ncoef doubles); points at (px[i stride],
+// py[i stride], pz[i stride]); out[perm ? perm[i] : i]; cws and abws hold
+// ncoef complex values each (T2 copies of the coefficients and of the
+// recurrence factors a_rec, b_rec).
+struct ForwardArgs {
+  int N;
+  bool mixed;
+  const double* coeffs;
+  const double *a_rec, *b_rec;
+  void* cws;
+  void* abws;
+  const double *px, *py, *pz;
+  int64_t stride, P;
+  const uint32_t* perm;
+  double* out;
+  int num_sms;
+};
+void run_forward(const ForwardArgs& a, cudaStream_t s, int64_t* launches);
+
 // ---------------------------------------------------------------- voronoi.cu
 // Area of the spherical Voronoi cell of every point of g (FP32 area when
 // mixed, FP64 otherwise): written to out[perm[s]], sw[s] and swf[s] for the
