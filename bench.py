@@ -730,9 +730,10 @@ def run_ours(args):
 
     # ---- the forward transform F (hamls_forward) of the fit's coefficients at
     # the 4M nodes: CUDA events, L2 flushed between calls. FP32 ALU-bound: per
-    # node the (N+1)(N+2)/2 recurrence terms of about 9 FP32 flops each (the
-    # three-term step, the scale, two FMAs into the order's sum); peak = 148 SMs
-    # x 128 FP32 lanes x 2 flops x the SM clock seen during the run.
+    # node the (N+1)(N+2)/2 recurrence terms of 8 FP32 flops each (the
+    # three-term step: two products, a difference and the factor; two FMAs
+    # into the order's sum); peak = 148 SMs x 128 FP32 lanes x 2 flops x the
+    # SM clock seen during the run.
     def forward_leg(pl, coeffs, reps):
         try:
             pl.set_timing(False)
@@ -752,12 +753,12 @@ def run_ours(args):
             pl.sync(600000)
             ms = float(np.mean(ts))
             terms = (w.N + 1) * (w.N + 2) // 2
-            flops = 9.0 * terms * w.M
+            flops = 8.0 * terms * w.M
             res = vals.cpu().numpy() - (w.values if isinstance(w.values, np.ndarray) else w.values.cpu().numpy())
             return {"ms": ms, "points_per_s": w.M / (ms / 1000.0), "reps": reps,
                     "kernel": "forward_kernel<float> (+ coefficient and factor conversion)",
                     "roofline": {"bound": "alu", "achieved": flops / (ms / 1000.0) / 1e12, "unit": "TFLOP/s",
-                                 "flops_per_point": 9.0 * terms, "peak_note": "148 SMs x 128 FP32 lanes x 2 x SM clock"},
+                                 "flops_per_point": 8.0 * terms, "peak_note": "148 SMs x 128 FP32 lanes x 2 x SM clock"},
                     "residual_rms_over_data_rms": float(np.sqrt(np.mean(res ** 2)) /
                                                         np.sqrt(np.mean(np.asarray(w.values) ** 2)))}
         except Exception as e:                  # reported, never fatal to the headline line

@@ -8,16 +8,21 @@
 // same (m, l) sequence, so coefficients and recurrence factors are uniform
 // loads, each serving four recurrences.
 //
-// Per order m (FP64): the seed Pbar_m^m = Pbar_{m-1}^{m-1} * (-sqrt((2m+1)/(2m)) sin theta)
-// and e^{i m phi} by one rotation with e^{i phi} = (x + i y) / sin theta.
-// Per degree (T = float for mixed plans, double for FP64 plans): the
-// three-term recurrence Pbar_l^m = a_lm (t Pbar_{l-1}^m - b_lm Pbar_{l-2}^m)
-// (the plan's recurrence factors). Near the poles the seed falls far below
+// Everything in T (float for mixed plans, double for FP64 plans): per order m
+// the seed Pbar_m^m = Pbar_{m-1}^{m-1} * (-sqrt((2m+1)/(2m)) sin theta) and
+// e^{i m phi} by one rotation with e^{i phi} = (x + i y) / sin theta; per
+// degree the three-term recurrence Pbar_l^m = a_lm (t Pbar_{l-1}^m - b_lm Pbar_{l-2}^m)
+// (the plan's recurrence factors). In FP32 a term of order m and degree l
+// carries a relative error of about (m + (l - m)) 2^-24 <= N 2^-24 from the
+// seed chain, the rotation and the recurrence, inside the FP32 error bound of
+// the whole sum, 2 (N + 3) 2^-24 sum |terms|. Near the poles the seed falls far below
 // the FP32 range (sin theta = 0.1, m = 51: 1e-51) while Pbar_l^m climbs back
 // to O(1) by l = 512, so the value carries a binary exponent e: the true
-// value is p 2^e, p is rescaled by 2^60 whenever it leaves [2^-60, 2^60) on
-// the small side (seed) or the large side (recurrence, while e < 0), and a
-// term whose scale 2^e is below 2^-120 (so |term| < 2^-60 |fhat|) is skipped.
+// value is p 2^e; the seed is rescaled by 2^60 whenever it falls below 2^-60,
+// and the recurrence values, together with the order's sums kept in the same
+// frame, are rescaled by 2^-60 (checked every eight degrees) whenever they
+// pass 2^60 while e < 0. An order's sum enters f times 2^e (zero when
+// e <= -120: then every term is below 2^-60 |fhat|).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -79,11 +84,20 @@ __global__ void __launch_bounds__(256) forward_kernel(int N, const typename Vec2
   using T2 = typename Vec2<T>::t;
   constexpr int Q = FWD_PPT;
   extern __shared__ double fwd_smem[];
-  double* fm = fwd_smem;                            // -sqrt((2m+1)/(2m)), m = 1..N
+  T* fm = reinterpret_cast<T*>(fwd_smem);          // -sqrt((2m+1)/(2m)), m = 1..N
   T* g1 = reinterpret_cast<T*>(fwd_smem + N + 1);   // sqrt(2m+3): Pbar_{m+1}^m = g1 t Pbar_m^m
+  float* kb = reinterpret_cast<float*>(fwd_smem + 2 * (N + 1));   // the order bound's constant
   for (int m = threadIdx.x; m <= N; m += blockDim.x) {
-    fm[m] = m > 0 ? -sqrt((2.0 * m + 1.0) / (2.0 * m)) : 0.0;
+    fm[m] = (T)(m > 0 ? -sqrt((2.0 * m + 1.0) / (2.0 * m)) : 0.0);
     g1[m] = (T)sqrt(2.0 * m + 3.0);
+    // |Pbar_l^m(t)| <= sqrt((2l+1)/(4 pi)) s^m sqrt((l+m)!/(l-m)!) / (2^m m!)
+    // (|d^m P_l / dt^m| is largest at t = 1, where it is (l+m)!/(2^m m! (l-m)!)),
+    // increasing in l: log2 of the bound at l = N, less m log2 s, plus
+    // log2(N + 1) for the order's number of terms
+    const double LN2 = 0.69314718055994530942;
+    kb[m] = (float)(0.5 * log2((2.0 * N + 1.0) / (4.0 * 3.14159265358979323846)) +
+                    (0.5 * (lgamma(N + m + 1.0) - lgamma(N - m + 1.0)) - lgamma(m + 1.0)) / LN2 - m +
+                    log2(N + 1.0));
   }
   __syncthreads();
   const T HI = (T)1.152921504606846976e18;         // 2^60
@@ -91,8 +105,8 @@ __global__ void __launch_bounds__(256) forward_kernel(int N, const typename Vec2
   const int64_t groups = (P + Q - 1) / Q;
   for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < groups;
        gi += (int64_t)gridDim.x * blockDim.x) {
-    double s[Q], cph[Q], sph[Q], pmm[Q], cr[Q], sr[Q], f[Q];
-    T t[Q];
+    T s[Q], cph[Q], sph[Q], pmm[Q], cr[Q], sr[Q], f[Q], t[Q];
+    float ls[Q];                                    // log2 sin theta (-inf at the poles)
     int em[Q];
     bool on[Q];
 #pragma unroll
@@ -101,40 +115,48 @@ __global__ void __launch_bounds__(256) forward_kernel(int N, const typename Vec2
       on[q] = i < P;
       const int64_t ii = on[q] ? i : gi * Q;
       const double x = px[ii * stride], y = py[ii * stride], z = pz[ii * stride];
-      s[q] = sqrt(x * x + y * y);
-      cph[q] = s[q] > 0.0 ? x / s[q] : 1.0;
-      sph[q] = s[q] > 0.0 ? y / s[q] : 0.0;
+      const double sd = sqrt(x * x + y * y);
+      s[q] = (T)sd;
+      ls[q] = on[q] ? log2f((float)sd) : -__int_as_float(0x7f800000);
+      cph[q] = sd > 0.0 ? (T)(x / sd) : T(1);
+      sph[q] = sd > 0.0 ? (T)(y / sd) : T(0);
       t[q] = (T)z;
-      pmm[q] = 0.28209479177387814347;              // Pbar_0^0 = 1 / sqrt(4 pi)
+      pmm[q] = (T)0.28209479177387814347;           // Pbar_0^0 = 1 / sqrt(4 pi)
       em[q] = 0;                                    // Pbar_m^m = pmm 2^em
-      cr[q] = 1.0;                                  // e^{i m phi}
-      sr[q] = 0.0;
-      f[q] = 0.0;
+      cr[q] = T(1);                                 // e^{i m phi}
+      sr[q] = T(0);
+      f[q] = T(0);
     }
     for (int m = 0; m <= N; ++m) {
       const size_t row0 = (size_t)m * (N + 1) - (size_t)m * (m - 1) / 2;
-      T p1[Q], p2[Q], sc[Q], accr[Q], acci[Q];
+      // values and the order's sums in the frame 2^e of the point's seed
+      T p1[Q], p2[Q], accr[Q], acci[Q];
       int e[Q];
       const T2 c0 = cf[row0];
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         if (m > 0) {
           pmm[q] *= fm[m] * s[q];
-          if (pmm[q] != 0.0 && fabs(pmm[q]) < 8.673617379884035472e-19) {
-            pmm[q] *= 1.152921504606846976e18;
+          if (pmm[q] != T(0) && fabs(pmm[q]) < LO) {
+            pmm[q] *= HI;
             em[q] -= 60;
           }
-          const double c2 = cr[q] * cph[q] - sr[q] * sph[q];
+          const T c2 = cr[q] * cph[q] - sr[q] * sph[q];
           sr[q] = sr[q] * cph[q] + cr[q] * sph[q];
           cr[q] = c2;
         }
         e[q] = em[q];
-        sc[q] = scale_of<T>(e[q]);
         p2[q] = T(0);
-        p1[q] = (T)pmm[q];
-        accr[q] = c0.x * (p1[q] * sc[q]);
-        acci[q] = c0.y * (p1[q] * sc[q]);
+        p1[q] = pmm[q];
+        accr[q] = c0.x * p1[q];
+        acci[q] = c0.y * p1[q];
       }
+      // an order whose bound stays below 2^-80 for all of the thread's points
+      // contributes less than 2^-80 max |fhat| to each of them: skipped
+      bool need = m == 0;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) need |= (float)m * ls[q] + kb[m] >= -80.f;
+      if (!need) continue;
       if (m < N) {
         const T2 c1 = cf[row0 + 1];
 #pragma unroll
@@ -142,71 +164,65 @@ __global__ void __launch_bounds__(256) forward_kernel(int N, const typename Vec2
           const T p = g1[m] * t[q] * p1[q];
           p2[q] = p1[q];
           p1[q] = p;
-          accr[q] += c1.x * (p1[q] * sc[q]);
-          acci[q] += c1.y * (p1[q] * sc[q]);
+          accr[q] += c1.x * p;
+          acci[q] += c1.y * p;
         }
       }
-      // careful phase: while a point's value carries a negative exponent
+      // eight degrees per step, two at a time so that the recurrence
+      // alternates between the two registers; a value (and the sums) leaving
+      // [.., 2^60) while its frame is below 1 is rescaled once per step (the
+      // growth over eight degrees is below 2^38, far inside the FP32 range)
       int l = m + 2;
-      bool neg = false;
+      for (; l + 7 <= N; l += 8) {
+        const size_t o = row0 + (size_t)(l - m);
 #pragma unroll
-      for (int q = 0; q < Q; ++q) neg |= e[q] < 0;
-      for (; neg && l <= N; ++l) {
+        for (int k = 0; k < 8; k += 2) {
+          const T2 fa = ab[o + k], fb = ab[o + k + 1];
+          const T2 ca = cf[o + k], cb = cf[o + k + 1];
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            p2[q] = fa.x * (t[q] * p1[q] - fa.y * p2[q]);
+            accr[q] += ca.x * p2[q];
+            acci[q] += ca.y * p2[q];
+            p1[q] = fb.x * (t[q] * p2[q] - fb.y * p1[q]);
+            accr[q] += cb.x * p1[q];
+            acci[q] += cb.y * p1[q];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          if (e[q] < 0 && fabs(p1[q]) > HI) {
+            p1[q] *= LO;
+            p2[q] *= LO;
+            accr[q] *= LO;
+            acci[q] *= LO;
+            e[q] += 60;
+          }
+        }
+      }
+      for (; l <= N; ++l) {
         const size_t o = row0 + (size_t)(l - m);
         const T2 f2 = ab[o];
         const T2 c = cf[o];
-        neg = false;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           const T p = f2.x * (t[q] * p1[q] - f2.y * p2[q]);
           p2[q] = p1[q];
           p1[q] = p;
-          if (e[q] < 0 && fabs(p1[q]) > HI) {
-            p1[q] *= LO;
-            p2[q] *= LO;
-            e[q] += 60;
-            sc[q] = scale_of<T>(e[q]);
-          }
-          accr[q] += c.x * (p1[q] * sc[q]);
-          acci[q] += c.y * (p1[q] * sc[q]);
-          neg |= e[q] < 0;
-        }
-      }
-      // plain phase (every exponent 0, scale 1), two degrees per step so that
-      // the recurrence alternates between the two registers
-      for (; l + 1 <= N; l += 2) {
-        const size_t o = row0 + (size_t)(l - m);
-        const T2 fa = ab[o], fb = ab[o + 1];
-        const T2 ca = cf[o], cb = cf[o + 1];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          p2[q] = fa.x * (t[q] * p1[q] - fa.y * p2[q]);
-          accr[q] += ca.x * p2[q];
-          acci[q] += ca.y * p2[q];
-          p1[q] = fb.x * (t[q] * p2[q] - fb.y * p1[q]);
-          accr[q] += cb.x * p1[q];
-          acci[q] += cb.y * p1[q];
-        }
-      }
-      if (l <= N) {
-        const size_t o = row0 + (size_t)(l - m);
-        const T2 f2 = ab[o];
-        const T2 c = cf[o];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          const T p = f2.x * (t[q] * p1[q] - f2.y * p2[q]);
           accr[q] += c.x * p;
           acci[q] += c.y * p;
         }
       }
 #pragma unroll
-      for (int q = 0; q < Q; ++q)
-        f[q] += m == 0 ? (double)accr[q] : 2.0 * ((double)accr[q] * cr[q] - (double)acci[q] * sr[q]);
+      for (int q = 0; q < Q; ++q) {
+        const T sc = scale_of<T>(e[q]);
+        f[q] += sc * (m == 0 ? accr[q] : T(2) * (accr[q] * cr[q] - acci[q] * sr[q]));
+      }
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int64_t i = gi * Q + q;
-      if (on[q]) out[perm ? (int64_t)perm[i] : i] = f[q];
+      if (on[q]) out[perm ? (int64_t)perm[i] : i] = (double)f[q];
     }
   }
 }
@@ -214,7 +230,7 @@ __global__ void __launch_bounds__(256) forward_kernel(int N, const typename Vec2
 void run_forward(const ForwardArgs& a, cudaStream_t s, int64_t* launches) {
   const int64_t ncoef = (int64_t)(a.N + 1) * (a.N + 2) / 2;
   const int cb = (int)((ncoef + 255) / 256);
-  const size_t smem = (size_t)(a.N + 1) * (sizeof(double) + sizeof(double));
+  const size_t smem = (size_t)(a.N + 1) * (sizeof(double) + sizeof(double) + sizeof(float));
   const int64_t want = ((a.P + FWD_PPT - 1) / FWD_PPT + 255) / 256;
   const int blocks = (int)(want < (int64_t)a.num_sms * 8 ? (want < 1 ? 1 : want) : (int64_t)a.num_sms * 8);
   if (a.mixed) {
