@@ -41,9 +41,17 @@ struct Vec2<double> {
   using t = double2;
 };
 
+// 2^e for the exponent frames (e = 0, -60, -120, ...), zero at and below
+// 2^-120; built from the bit pattern (no FP64 operation)
 template <typename T>
-__device__ __forceinline__ T scale_of(int e) {
-  return e <= -120 ? T(0) : (T)ldexp(1.0, e);
+__device__ __forceinline__ T scale_of(int e);
+template <>
+__device__ __forceinline__ float scale_of<float>(int e) {
+  return e <= -120 ? 0.f : __int_as_float((e + 127) << 23);
+}
+template <>
+__device__ __forceinline__ double scale_of<double>(int e) {
+  return e <= -120 ? 0.0 : __longlong_as_double((long long)(e + 1023) << 52);
 }
 
 }  // namespace
