@@ -24,15 +24,22 @@ def load_bench():
 
 
 def test_sampled_estimate_matches_a_whole_fit():
+    # best of three on both sides: a shared host's load spikes only ever make
+    # a timing longer, so the minimum is the figure to compare
     bench = load_bench()
     w = workload("s2_n16_k2_m5k")
-    est = bench.OracleBaseline(w, 96).estimate()
-    assert est["value"] > 0
-    t0 = time.perf_counter()
-    O.hamls(w.nodes, w.values, w.N, w.K, O.Params())
-    whole = time.perf_counter() - t0
-    ratio = (1.0 / est["value"]) / whole
-    assert 0.7 < ratio < 1.4, (ratio, est["sample"], whole)
+    ob = bench.OracleBaseline(w, 96)
+    ests = [ob.estimate() for _ in range(3)]
+    assert all(e["value"] > 0 for e in ests)
+    est_s = min(1.0 / e["value"] for e in ests)
+    wholes = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        O.hamls(w.nodes, w.values, w.N, w.K, O.Params())
+        wholes.append(time.perf_counter() - t0)
+    whole = min(wholes)
+    ratio = est_s / whole
+    assert 0.7 < ratio < 1.4, (ratio, ests[0]["sample"], wholes)
 
 
 def test_all_cores_estimate_is_bounded_by_the_cores():
