@@ -456,8 +456,9 @@ def many_sets_leg(h, plan, w, y, flush, stream, B, steps, warmup, peaks, truth_e
     mt = -(-2 * B // 128) * 128
     flops_exec = 3 * 2 * rows_pad * kp * mt
     flops_alg = 2 * ncoef * hc * 2 * B
-    # DRAM bytes as stored: matrix hi + lo, folded spectra hi + lo, coefficients out
-    bytes_alg = 2 * ncoef * hcp * 4 + 2 * (2 * (N + 1)) * (2 * B) * hcp * 4 + B * ncoef * 16
+    # algorithmic bytes: the FP32 matrix and folded spectra once each (the
+    # kernel splits them for 3xTF32 in shared memory), the coefficients out
+    bytes_alg = ncoef * hcp * 4 + (2 * (N + 1)) * (2 * B) * hcp * 4 + B * ncoef * 16
     tf32_peak = float(peaks.get("bf16_tflops", 1800.0)) * 0.5
     quad = {"sets": B, "value": B * len(ts) / (float(ts.sum()) / 1000.0), "unit": "grids/s",
             "ms_per_call": float(ts.mean()), "spectra_ms": st["fft"], "tensor_ms": st["legendre"],

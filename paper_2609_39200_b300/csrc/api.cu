@@ -95,7 +95,7 @@ struct hamls_plan_s {
   float *rb_yo = nullptr, *rb_yT = nullptr, *rb_fT = nullptr;
   double* rb_f = nullptr;
   float2* batch_F = nullptr;
-  float *batch_G = nullptr, *batch_Glo = nullptr;
+  float* batch_G = nullptr;
   unsigned* batch_err = nullptr;
   // scattered nodes: the cell structure (B bands, P cells per band) follows
   // the current node count; Bcap is the largest one the arena holds
@@ -893,21 +893,20 @@ static hamls_status quad_batch_mixed(hamls_plan_s* P, const double* fgrid, doubl
     }
     const size_t bF = ((size_t)B * (N + 1) * (N + 1) * sizeof(float2) + 255) & ~size_t(255);
     const size_t bG = ((size_t)2 * (N + 1) * 2 * B * P->g.hcp * sizeof(float) + 255) & ~size_t(255);
-    HAMLS_TRY(cudaMalloc(&P->batch_mem, bF + 2 * bG + 256));
+    HAMLS_TRY(cudaMalloc(&P->batch_mem, bF + bG + 256));
     P->batch_F = reinterpret_cast<float2*>(P->batch_mem);
     P->batch_G = reinterpret_cast<float*>(reinterpret_cast<char*>(P->batch_mem) + bF);
-    P->batch_Glo = reinterpret_cast<float*>(reinterpret_cast<char*>(P->batch_mem) + bF + bG);
-    P->batch_err = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(P->batch_mem) + bF + 2 * bG);
+    P->batch_err = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(P->batch_mem) + bF + bG);
     P->batch_cap = B;
   }
   HAMLS_TRY(cudaMemsetAsync(P->batch_err, 0, sizeof(unsigned), s));
   stage_begin(P, 6, s);
-  cudaError_t e = run_spectra_batch(P->g, P->radices, P->nrad, fgrid, B, P->batch_F, P->batch_G, P->batch_Glo, s,
+  cudaError_t e = run_spectra_batch(P->g, P->radices, P->nrad, fgrid, B, P->batch_F, P->batch_G, s,
                                     &P->launches);
   stage_end(P, 6, s);
   if (e != cudaSuccess) return cuda_status(e);
   stage_begin(P, 7, s);
-  e = tc_legendre(P->g, P->batch_G, P->batch_Glo, B, P->tables->jobs, P->tables->njobs, coeffs, P->batch_err, s,
+  e = tc_legendre(P->g, P->batch_G, B, P->tables->jobs, P->tables->njobs, coeffs, P->batch_err, s,
                   &P->launches);
   stage_end(P, 7, s);
   if (e != cudaSuccess) return cuda_status(e);

@@ -52,7 +52,6 @@ struct GridTables {
   double *a_rec, *b_rec;        // packed (N+1)(N+2)/2 recurrence coefficients
   double* A64;                  // folded Legendre quadrature matrix, ncoef x hc
   float* A32;
-  float *A32hi, *A32lo;         // A32 split for 3xTF32 products: hi exact in TF32, lo = A32 - hi
   double2* W64;                 // FFT twiddles exp(-2 pi i j / L), L = 2N+2
   float2* W32;
   float *tf, *sf, *cpf, *spf;   // FP32 copies of t, s, cphi, sphi (FP32 paths)
@@ -80,12 +79,10 @@ struct TcJob {
 // count only): one per order m, parity and block of at most 256 degrees.
 int tc_legendre_jobs(int N, TcJob* out);
 // coeffs (B x ncoef complex, each set packed as hamls_fit) of the B value
-// sets whose folded spectra are Ghi + Glo: 2(N+1) blocks (order m, parity)
-// of 2B rows (set b: real part row 2b, imaginary 2b+1) of hcp FP32 (hc used)
-cudaError_t tc_legendre(const GridTables& g, const float* Ghi, const float* Glo, int B, const TcJob* jobs, int njobs,
-                        double* coeffs, unsigned* err, cudaStream_t s, int64_t* launches);
-// x_hi (the low 13 mantissa bits cleared: exact in TF32) and x_lo = x - x_hi
-void split_tf32(const float* x, size_t n, float* hi, float* lo, cudaStream_t s, int64_t* launches);
+// sets whose folded spectra are G: 2(N+1) blocks (order m, parity) of 2B
+// rows (set b: real part row 2b, imaginary 2b+1) of hcp FP32 (hc used)
+cudaError_t tc_legendre(const GridTables& g, const float* G, int B, const TcJob* jobs, int njobs, double* coeffs,
+                        unsigned* err, cudaStream_t s, int64_t* launches);
 
 // ----------------------------------------------------------------- tables.cu
 struct SharedTables {
@@ -222,9 +219,9 @@ struct QuadArgs {
 void run_quadrature(const QuadArgs& a, bool mixed, cudaStream_t s, int64_t* launches, int part = 3);
 // step 3 of B value sets (mixed form), first part: ring FFTs of fgrid
 // (B x M_Q, set b at b M_Q) into F (B x (N+1)^2 complex FP32) and the folded
-// spectra split for 3xTF32 (Ghi, Glo); tc_legendre then contracts them
+// spectra G (FP32); tc_legendre then contracts them
 cudaError_t run_spectra_batch(const GridTables& g, const int* radices, int nrad, const double* fgrid, int B,
-                              float2* F, float* Ghi, float* Glo, cudaStream_t s, int64_t* launches);
+                              float2* F, float* G, cudaStream_t s, int64_t* launches);
 
 // ---------------------------------------------------------------- forward.cu
 // The forward transform f(x) = (F fhat)(x) at P points (Sec. 1): coeffs

@@ -228,12 +228,11 @@ static void launch_quad(const QuadArgs& a, const typename C2<T>::t* W, const T* 
 // The folded spectra of a batch, the A operand of the tensor-core Legendre
 // contraction: for value set b, order m and column c < hc,
 //   E = F_c(m) + F_{N-c}(m),  O = F_c(m) - F_{N-c}(m)   (E = O = F_c(m) if c = N - c),
-// stored as G[(2m + p) * 2B + 2b + {0: re, 1: im}][c], p = 0 for E, 1 for O.
+// stored as G[(2m + p) * 2B + 2b + {0: re, 1: im}][c], p = 0 for E, 1 for O
+// (FP32; the tensor-core kernel splits it for 3xTF32 as it reads it).
 // A 32 x 32 tile of (c, m) per block: reads along m, writes along c.
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
-
 __global__ void __launch_bounds__(256) fold_spectra_kernel(const float2* __restrict__ F, int N, int hc, int hcp,
-                                                           int B, float* __restrict__ Ghi, float* __restrict__ Glo) {
+                                                           int B, float* __restrict__ G) {
   __shared__ float2 E[32][33], O[32][33];
   const int b = blockIdx.z, m0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   const float2* Fb = F + (size_t)b * (N + 1) * (N + 1);
@@ -261,34 +260,15 @@ __global__ void __launch_bounds__(256) fold_spectra_kernel(const float2* __restr
     const int m = m0 + r, c = c0 + tx;
     if (m > N || c >= hc) continue;
     const size_t o = (size_t)(2 * m) * ps + (size_t)(2 * b) * rs + c;
-    const float v[4] = {E[r][tx].x, E[r][tx].y, O[r][tx].x, O[r][tx].y};
-    const size_t at[4] = {o, o + rs, o + ps, o + ps + rs};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float hi = tf32_hi(v[q]);
-      Ghi[at[q]] = hi;
-      Glo[at[q]] = v[q] - hi;
-    }
+    G[o] = E[r][tx].x;
+    G[o + rs] = E[r][tx].y;
+    G[o + ps] = O[r][tx].x;
+    G[o + ps + rs] = O[r][tx].y;
   }
-}
-
-__global__ void split_tf32_kernel(const float* __restrict__ x, size_t n, float* __restrict__ hi,
-                                  float* __restrict__ lo) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const float h = tf32_hi(x[i]);
-    hi[i] = h;
-    lo[i] = x[i] - h;
-  }
-}
-
-void split_tf32(const float* x, size_t n, float* hi, float* lo, cudaStream_t s, int64_t* launches) {
-  const size_t blocks = (n + 255) / 256;
-  split_tf32_kernel<<<(int)(blocks < 65535 ? blocks : 65535), 256, 0, s>>>(x, n, hi, lo);
-  ++*launches;
 }
 
 cudaError_t run_spectra_batch(const GridTables& g, const int* radices, int nrad, const double* fgrid, int B,
-                              float2* F, float* Ghi, float* Glo, cudaStream_t s, int64_t* launches) {
+                              float2* F, float* G, cudaStream_t s, int64_t* launches) {
   const int N = g.N, L = 2 * N + 2;
   QuadArgs qa;
   memset(&qa, 0, sizeof(qa));
@@ -298,8 +278,7 @@ cudaError_t run_spectra_batch(const GridTables& g, const int* radices, int nrad,
   static unsigned done_fft = 0;
   set_smem_attr_once((const void*)ring_fft_kernel<float>, 200 * 1024, &done_fft);
   ring_fft_kernel<float><<<dim3((N + 2) / 2, B), 256, 3 * (size_t)L * sizeof(float2), s>>>(fgrid, N, qa, g.W32, F);
-  fold_spectra_kernel<<<dim3((N + 1 + 31) / 32, (g.hc + 31) / 32, B), 256, 0, s>>>(F, N, g.hc, g.hcp, B, Ghi,
-                                                                                    Glo);
+  fold_spectra_kernel<<<dim3((N + 1 + 31) / 32, (g.hc + 31) / 32, B), 256, 0, s>>>(F, N, g.hc, g.hcp, B, G);
   *launches += 2;
   return cudaGetLastError();
 }

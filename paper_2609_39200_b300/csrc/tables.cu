@@ -45,8 +45,6 @@ size_t carve_tables(GridTables& g, char* base, bool mixed, int njobs, TcJob** jo
   g.b_rec = reinterpret_cast<double*>(take(sizeof(double) * ncoef));
   g.A64 = mixed ? nullptr : reinterpret_cast<double*>(take(sizeof(double) * ncoef * g.hc));
   g.A32 = mixed ? reinterpret_cast<float*>(take(sizeof(float) * ncoef * g.hcp)) : nullptr;
-  g.A32hi = mixed ? reinterpret_cast<float*>(take(sizeof(float) * ncoef * g.hcp)) : nullptr;
-  g.A32lo = mixed ? reinterpret_cast<float*>(take(sizeof(float) * ncoef * g.hcp)) : nullptr;
   g.W64 = reinterpret_cast<double2*>(take(sizeof(double2) * L));
   g.W32 = reinterpret_cast<float2*>(take(sizeof(float2) * L));
   g.tf = reinterpret_cast<float*>(take(sizeof(float) * (N + 1)));
@@ -107,10 +105,6 @@ SharedTables* tables_acquire(int N, bool mixed, cudaStream_t s, int64_t* launche
     return nullptr;
   }
   build_grid_tables(t->g, mixed, !mixed, s, launches);
-  if (mixed) {
-    const size_t ncoef = (size_t)(N + 1) * (N + 2) / 2;
-    split_tf32(t->g.A32, ncoef * t->g.hcp, t->g.A32hi, t->g.A32lo, s, launches);
-  }
   if (t->njobs > 0) {
     std::vector<TcJob> hj((size_t)t->njobs);
     tc_legendre_jobs(N, hj.data());

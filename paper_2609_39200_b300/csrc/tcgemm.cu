@@ -12,13 +12,12 @@
 // matrix (degrees x latitudes).
 //
 // One CTA (4 warps) computes a 128 x NT tile of D (NT <= 256 columns of
-// tensor memory). The hi and lo parts of both operands are split once, when
-// they are written (the quadrature matrix at table build, the spectra by
-// fold_spectra_kernel), and held in global memory. Per K step of 32 (one
-// 128-byte row of a swizzled tile) one thread has TMA bring the four tiles
-// (A hi, A lo, B hi, B lo; boxes of 32 rows x 32 FP32, 128-byte swizzle) into
-// one of two shared-memory stages and issues the 4 x 3 tcgen05.mma of the
-// step; tcgen05.commit frees the stage for the TMA two steps ahead. The
+// tensor memory). Both operands are held in global memory as FP32 and cross
+// HBM once: per K step of 32 (one 128-byte row of a swizzled tile) one thread
+// has TMA bring the two FP32 tiles (boxes of 32 rows x 32 FP32, 128-byte
+// swizzle) into one of two shared-memory stages, all threads split them into
+// hi (in place) and lo tiles, and the thread issues the 4 x 3 tcgen05.mma of
+// the step; tcgen05.commit frees the stage for the TMA two steps ahead. The
 // epilogue reads D from tensor memory (warp w owns lanes 32w..32w+31) and
 // hands 16 columns at a time to the caller's epilogue.
 //
@@ -109,19 +108,32 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // ------------------------------------------------------------ the kernel
-// The main loop runs on one thread: per K step it waits for the stage's four
-// tiles (A hi, A lo, B hi, B lo), issues the 4 x 3 products and commits them
-// to the stage's "empty" barrier, then refills the stage two steps ahead once
-// the products have read it. The other threads wait for the final commit.
-// The result goes from tensor memory to shared memory (transposed: column n
-// of D at S + n * TC_LDS) and the epilogue writes it out from there.
+// Per K step every thread waits for the stage's two FP32 tiles (A, B), then
+// splits its share of them in shared memory: hi (the value with its 13 low
+// mantissa bits cleared, exact in TF32) in place, lo = value - hi into the
+// stage's lo tiles at the same byte offsets (so the 128-byte swizzle carries
+// over), and fences its writes for the tensor core. After a block barrier
+// thread 0 issues the 4 x 3 products and commits them to the stage's "empty"
+// barrier, then refills the stage two steps ahead once the products have read
+// it. A wait that gives up (or a refill that could not be issued) ends the
+// loop for all threads at the next step. The result goes from tensor memory
+// to shared memory (transposed: column n of D at S + n * TC_LDS) and the
+// epilogue writes it out from there.
 constexpr int TC_LDS = 129;
 
+__device__ __forceinline__ void tf32_split4(float4* hi, float4* lo) {
+  float4 v = *hi, h;
+  h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+  h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+  h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+  h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+  *hi = h;
+  *lo = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+}
+
 template <class Epi>
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapAh,
-                                                                 const __grid_constant__ CUtensorMap mapAl,
-                                                                 const __grid_constant__ CUtensorMap mapBh,
-                                                                 const __grid_constant__ CUtensorMap mapBl,
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                                 const __grid_constant__ CUtensorMap mapB,
                                                                  const TcJob* __restrict__ jobs, int K, Epi epi,
                                                                  unsigned* err) {
   extern __shared__ unsigned char tc_raw[];
@@ -138,7 +150,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
   job.a_y += 128 * (int)blockIdx.y;
   const int KT = (K + TC_BK - 1) / TC_BK;
   const int nb = job.nt / TC_BOX;
-  const uint32_t stage_bytes = 2u * (uint32_t)(128 / TC_BOX + nb) * TC_BOX * TC_BK * 4;
+  const uint32_t stage_bytes = (uint32_t)(128 / TC_BOX + nb) * TC_BOX * TC_BK * 4;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
@@ -154,48 +166,54 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     mbar_init(done, 1);
     *bad = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    prefetch_map(&mapAh);
-    prefetch_map(&mapAl);
-    prefetch_map(&mapBh);
-    prefetch_map(&mapBl);
+    prefetch_map(&mapA);
+    prefetch_map(&mapB);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  // lanes 1..31 of warp 0 park at the warp barrier below (not spinning on
-  // the mbarrier beside the thread that drives the pipeline)
-  if (tid == 0) {
-    auto tile = [&](int s, int which) { return sm + s * TC_STAGE + which * TC_TILE_A; };   // A hi, A lo
-    auto tileB = [&](int s, int which) { return sm + s * TC_STAGE + 2 * TC_TILE_A + which * TC_TILE_B; };
-    auto issue = [&](int kt, int s) {
-      mbar_expect_tx(&full[s], stage_bytes);
-      for (int r = 0; r < 128 / TC_BOX; ++r) {
-        tma_load_3d(tile(s, 0) + r * TC_BOX * TC_BK * 4, &mapAh, kt * TC_BK, job.a_y + r * TC_BOX, job.a_z, &full[s]);
-        tma_load_3d(tile(s, 1) + r * TC_BOX * TC_BK * 4, &mapAl, kt * TC_BK, job.a_y + r * TC_BOX, job.a_z, &full[s]);
-      }
-      for (int r = 0; r < nb; ++r) {
-        tma_load_3d(tileB(s, 0) + r * TC_BOX * TC_BK * 4, &mapBh, kt * TC_BK, job.b_y + r * TC_BOX, 0, &full[s]);
-        tma_load_3d(tileB(s, 1) + r * TC_BOX * TC_BK * 4, &mapBl, kt * TC_BK, job.b_y + r * TC_BOX, 0, &full[s]);
-      }
-    };
-    int loads[2] = {0, 0};
+  // stage s: A (hi in place) | A lo | B (hi in place) | B lo
+  auto tileA = [&](int s, int which) { return sm + s * TC_STAGE + which * TC_TILE_A; };
+  auto tileB = [&](int s, int which) { return sm + s * TC_STAGE + 2 * TC_TILE_A + which * TC_TILE_B; };
+  auto issue = [&](int kt, int s) {
+    mbar_expect_tx(&full[s], stage_bytes);
+    for (int r = 0; r < 128 / TC_BOX; ++r)
+      tma_load_3d(tileA(s, 0) + r * TC_BOX * TC_BK * 4, &mapA, kt * TC_BK, job.a_y + r * TC_BOX, job.a_z, &full[s]);
+    for (int r = 0; r < nb; ++r)
+      tma_load_3d(tileB(s, 0) + r * TC_BOX * TC_BK * 4, &mapB, kt * TC_BK, job.b_y + r * TC_BOX, 0, &full[s]);
+  };
+  int loads[2] = {0, 0};                            // thread 0's count of the loads issued per stage
+  if (tid == 0)
     for (int kt = 0; kt < KT && kt < 2; ++kt) {
       issue(kt, kt);
       ++loads[kt];
     }
-    const uint32_t idesc = tf32_idesc(job.nt);
-    bool ok = true;
-    for (int kt = 0; kt < KT && ok; ++kt) {
-      const int s = kt & 1;
-      const uint32_t ph = (uint32_t)(kt >> 1) & 1u;
-      if (!mbar_wait_bounded(&full[s], ph)) {
-        ok = false;
-        break;
-      }
+  const uint32_t idesc = tf32_idesc(job.nt);
+  int consumed = 0;                                 // K steps whose stage every thread has waited for
+  for (int kt = 0; kt < KT; ++kt) {
+    const int s = kt & 1;
+    const uint32_t ph = (uint32_t)(kt >> 1) & 1u;
+    const bool fail = !mbar_wait_bounded(&full[s], ph);
+    if (__syncthreads_or(fail || *bad)) {
+      if (tid == 0) *bad = 1;
+      break;
+    }
+    consumed = kt + 1;
+    {
+      float4* ah = reinterpret_cast<float4*>(tileA(s, 0));
+      float4* al = reinterpret_cast<float4*>(tileA(s, 1));
+      for (int i = tid; i < 128 * TC_BK / 4; i += TC_THREADS) tf32_split4(ah + i, al + i);
+      float4* bh = reinterpret_cast<float4*>(tileB(s, 0));
+      float4* bl = reinterpret_cast<float4*>(tileB(s, 1));
+      for (int i = tid; i < job.nt * TC_BK / 4; i += TC_THREADS) tf32_split4(bh + i, bl + i);
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
       tc_fence_after();
-      const uint32_t a_hi = smem_addr(tile(s, 0)), a_lo = smem_addr(tile(s, 1));
+      const uint32_t a_hi = smem_addr(tileA(s, 0)), a_lo = smem_addr(tileA(s, 1));
       const uint32_t b_hi = smem_addr(tileB(s, 0)), b_lo = smem_addr(tileB(s, 1));
 #pragma unroll
       for (int k = 0; k < TC_BK / 8; ++k) {
@@ -209,24 +227,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       mma_commit(&empty[s]);
       if (kt + 2 < KT) {
         // the stage is free once these products have read it
-        if (!mbar_wait_bounded(&empty[s], ph)) {
-          ok = false;
-          break;
+        if (mbar_wait_bounded(&empty[s], ph)) {
+          issue(kt + 2, s);
+          ++loads[s];
+        } else {
+          *bad = 1;                                 // seen by every thread at the next step
         }
-        issue(kt + 2, s);
-        ++loads[s];
       }
     }
+  }
+  if (tid == 0) {
     // the final commit covers every product issued
     mma_commit(done);
-    if (!ok) {
-      *bad = 1;
-      // wait (bounded) for every stage still loading before the CTA may exit
-      for (int s = 0; s < 2; ++s)
-        if (loads[s] > 0) (void)mbar_wait_bounded(&full[s], (uint32_t)(loads[s] - 1) & 1u);
+    if (*bad) {
+      // wait (bounded) for every load issued but not yet waited for before the CTA may exit
+      for (int kt = consumed; kt < consumed + 2 && kt < KT; ++kt) {
+        const int s = kt & 1;
+        if (loads[s] > (kt >> 1)) (void)mbar_wait_bounded(&full[s], (uint32_t)(kt >> 1) & 1u);
+      }
     }
   }
-  if (warp == 0) __syncwarp();
   if (!mbar_wait_bounded(done, 0)) atomicExch(bad, 1);
   tc_fence_after();
   __syncthreads();
@@ -294,8 +314,7 @@ static cudaError_t tc_launch(const CUtensorMap* maps, const TcJob* jobs, int njo
                              unsigned* err, cudaStream_t s) {
   static unsigned done = 0;
   set_smem_attr_once((const void*)tc_gemm_kernel<Epi>, TC_SMEM, &done);
-  tc_gemm_kernel<Epi><<<dim3(njobs, mtiles), TC_THREADS, TC_SMEM, s>>>(maps[0], maps[1], maps[2], maps[3], jobs, K,
-                                                                       epi, err);
+  tc_gemm_kernel<Epi><<<dim3(njobs, mtiles), TC_THREADS, TC_SMEM, s>>>(maps[0], maps[1], jobs, K, epi, err);
   return cudaGetLastError();
 }
 
@@ -353,18 +372,16 @@ int tc_legendre_jobs(int N, TcJob* out) {
   return n;
 }
 
-cudaError_t tc_legendre(const GridTables& g, const float* Ghi, const float* Glo, int B, const TcJob* jobs, int njobs,
-                        double* coeffs, unsigned* err, cudaStream_t s, int64_t* launches) {
+cudaError_t tc_legendre(const GridTables& g, const float* G, int B, const TcJob* jobs, int njobs, double* coeffs,
+                        unsigned* err, cudaStream_t s, int64_t* launches) {
   const int N = g.N;
   const uint64_t ncoef = (uint64_t)(N + 1) * (N + 2) / 2;
-  CUtensorMap maps[4];
+  CUtensorMap maps[2];
   memset(maps, 0, sizeof(maps));
   const uint64_t ld = (uint64_t)g.hcp * 4;
   const uint64_t zs = (uint64_t)2 * (N + 1);
-  if (!tc_make_map(&maps[0], Ghi, (uint64_t)g.hc, (uint64_t)(2 * B), zs, ld, ld * 2 * B) ||
-      !tc_make_map(&maps[1], Glo, (uint64_t)g.hc, (uint64_t)(2 * B), zs, ld, ld * 2 * B) ||
-      !tc_make_map(&maps[2], g.A32hi, (uint64_t)g.hc, ncoef, 1, ld, ld * ncoef) ||
-      !tc_make_map(&maps[3], g.A32lo, (uint64_t)g.hc, ncoef, 1, ld, ld * ncoef))
+  if (!tc_make_map(&maps[0], G, (uint64_t)g.hc, (uint64_t)(2 * B), zs, ld, ld * 2 * B) ||
+      !tc_make_map(&maps[1], g.A32, (uint64_t)g.hc, ncoef, 1, ld, ld * ncoef))
     return cudaErrorInvalidValue;
   EpiLegendre epi{coeffs, N, 2 * B, (size_t)ncoef};
   ++*launches;
@@ -408,31 +425,22 @@ extern "C" hamls_status hamls_debug_tc_gemm(const float* A, const float* B, floa
       const int cols = N - j.b_y < TC_MAXN ? N - j.b_y : TC_MAXN;
       j.nt = (cols + 31) / 32 * 32;
     }
-  // the operands split into hi and lo on the device (scratch for this call)
-  const size_t na = (size_t)M * K, nbk = (size_t)N * K;
+  // scratch for this call: the job table and an error word (the kernel
+  // splits the FP32 operands into hi and lo as it reads them)
   auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-  const size_t bj = up(sizeof(TcJob) * njobs + 16), ba = up(na * 4), bb = up(nbk * 4);
+  const size_t bj = up(sizeof(TcJob) * njobs + 16);
   char* mem = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&mem, bj + 2 * ba + 2 * bb, stream);
+  cudaError_t e = cudaMallocAsync((void**)&mem, bj, stream);
   TcJob* dj = reinterpret_cast<TcJob*>(mem);
   unsigned* derr = reinterpret_cast<unsigned*>(mem + sizeof(TcJob) * njobs);
-  float* Ah = reinterpret_cast<float*>(mem + bj);
-  float* Al = reinterpret_cast<float*>(mem + bj + ba);
-  float* Bh = reinterpret_cast<float*>(mem + bj + 2 * ba);
-  float* Bl = reinterpret_cast<float*>(mem + bj + 2 * ba + bb);
-  int64_t launches = 0;
-  CUtensorMap maps[4];
+  CUtensorMap maps[2];
   memset(maps, 0, sizeof(maps));
   if (e == cudaSuccess) e = cudaMemcpyAsync(dj, hj, sizeof(TcJob) * njobs, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, 4, stream);
   if (e == cudaSuccess) {
-    split_tf32(A, na, Ah, Al, stream, &launches);
-    split_tf32(B, nbk, Bh, Bl, stream, &launches);
     const uint64_t ld = (uint64_t)K * 4;
-    if (!tc_make_map(&maps[0], Ah, (uint64_t)K, (uint64_t)M, 1, ld, ld * M) ||
-        !tc_make_map(&maps[1], Al, (uint64_t)K, (uint64_t)M, 1, ld, ld * M) ||
-        !tc_make_map(&maps[2], Bh, (uint64_t)K, (uint64_t)N, 1, ld, ld * N) ||
-        !tc_make_map(&maps[3], Bl, (uint64_t)K, (uint64_t)N, 1, ld, ld * N))
+    if (!tc_make_map(&maps[0], A, (uint64_t)K, (uint64_t)M, 1, ld, ld * M) ||
+        !tc_make_map(&maps[1], B, (uint64_t)K, (uint64_t)N, 1, ld, ld * N))
       e = cudaErrorInvalidValue;
   }
   EpiDense epi{C, M, N, N};
