@@ -38,14 +38,16 @@
 
 namespace hamls {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 320;           // warp 0 TMA, warp 1 MMA, warps 2-5 split, warps 6-9 epilogue
 constexpr int TC_BK = 32;                 // K per stage: one 128-byte swizzled row of FP32
 constexpr int TC_BOX = 32;                // rows per TMA box
 constexpr int TC_MAXN = 256;              // columns of D per CTA (tensor-memory columns)
 constexpr int TC_TILE_A = 128 * TC_BK * 4;              // 16 KB
 constexpr int TC_TILE_B = TC_MAXN * TC_BK * 4;          // 32 KB
-constexpr int TC_STAGE = 2 * TC_TILE_A + 2 * TC_TILE_B; // hi and lo of both: 96 KB
-constexpr int TC_SMEM = 2 * TC_STAGE + 1024 + 256;      // two stages, alignment, barriers
+constexpr int TC_STAGE = TC_TILE_A + TC_TILE_B;         // the FP32 tiles of one K step: 48 KB
+constexpr int TC_NST = 3;                               // stages in the ring
+constexpr int TC_SMEM = (TC_NST + 1) * TC_STAGE + 1024 + 256;   // ring, lo tiles, alignment, barriers
+constexpr int TC_TMEM_COLS = 2 * TC_MAXN;               // two accumulators
 
 // ------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
@@ -108,19 +110,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // ------------------------------------------------------------ the kernel
-// Per K step every thread waits for the stage's two FP32 tiles (A, B), then
-// splits its share of them in shared memory: hi (the value with its 13 low
-// mantissa bits cleared, exact in TF32) in place, lo = value - hi into the
-// stage's lo tiles at the same byte offsets (so the 128-byte swizzle carries
-// over), and fences its writes for the tensor core. After a block barrier
-// thread 0 issues the 4 x 3 products and commits them to the stage's "empty"
-// barrier, then refills the stage two steps ahead once the products have read
-// it. A wait that gives up (or a refill that could not be issued) ends the
-// loop for all threads at the next step. The result goes from tensor memory
-// to shared memory (transposed: column n of D at S + n * TC_LDS) and the
-// epilogue writes it out from there.
-constexpr int TC_LDS = 129;
-
+// Persistent: one CTA per SM walks the tiles t = block, block + grid, ...
+// with its warps in four roles, each counting the uses of the two stages and
+// the two tensor-memory accumulators the same way:
+//   warp 0 (one thread)  TMA: waits until a stage's products are done, then
+//                        loads the stage's two FP32 tiles (full[s]); three
+//                        stages in the ring;
+//   warps 2-5            split: wait for full[s] and for the lo tiles to be
+//                        free (lofree: the previous step's products are done),
+//                        split their share of the stage into hi (in place) and
+//                        lo (the one pair of lo tiles), fence the writes for
+//                        the tensor core, arrive on ready;
+//   warp 1 (one thread)  MMA: waits for an accumulator the epilogue has
+//                        emptied (tempty[a]), then per K step for ready: 4 x 3
+//                        products, commit to empty[s] and to lofree; after a
+//                        tile's last step, commit to tfull[a];
+//   warps 6-9            epilogue: wait for tfull[a], read the accumulator
+//                        (warp w owns tensor-memory lanes 32 (w mod 4) ...),
+//                        store through the caller's epilogue, arrive on
+//                        tempty[a].
+// So a tile's epilogue runs under the next tile's loads and products. A
+// fresh barrier counts its "previous" phase as complete, so a role waits for
+// parity (use & 1) ^ 1 before reusing what a use freed. Every wait is bounded:
+// a role that gives up raises the CTA's abort flag, which the others read
+// before each step; at the end the TMA thread waits (bounded) for the loads it
+// issued and the MMA thread for its products, then tensor memory is freed.
 __device__ __forceinline__ void tf32_split4(float4* hi, float4* lo) {
   float4 v = *hi, h;
   h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
@@ -131,40 +145,52 @@ __device__ __forceinline__ void tf32_split4(float4* hi, float4* lo) {
   *lo = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool aborted(const volatile int* f) { return *f != 0; }
+
 template <class Epi>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                                                                  const __grid_constant__ CUtensorMap mapB,
-                                                                 const TcJob* __restrict__ jobs, int K, Epi epi,
-                                                                 unsigned* err) {
+                                                                 const TcJob* __restrict__ jobs, int ntiles,
+                                                                 int mtiles, int K, Epi epi, unsigned* err) {
   extern __shared__ unsigned char tc_raw[];
   // stages on a 1024-byte boundary (the 128-byte swizzle repeats every 1024)
   const uint32_t base = smem_addr(tc_raw);
   unsigned char* sm = tc_raw + ((1024u - (base & 1023u)) & 1023u);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + 2 * TC_STAGE);
-  uint64_t* empty = full + 2;
-  uint64_t* done = full + 4;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 6);
-  int* bad = reinterpret_cast<int*>(full + 7);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + (TC_NST + 1) * TC_STAGE);
+  uint64_t* empty = full + TC_NST;
+  uint64_t* ready = empty + TC_NST;
+  uint64_t* lofree = ready + 1;
+  uint64_t* tfull = lofree + 1;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* done = tempty + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(done + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  TcJob job = jobs[blockIdx.x];
-  job.a_y += 128 * (int)blockIdx.y;
   const int KT = (K + TC_BK - 1) / TC_BK;
-  const int nb = job.nt / TC_BOX;
-  const uint32_t stage_bytes = (uint32_t)(128 / TC_BOX + nb) * TC_BOX * TC_BK * 4;
 
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
-                 "r"(TC_MAXN)
+                 "r"(TC_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < TC_NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
+    mbar_init(ready, 128);
+    mbar_init(lofree, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 128);
+    }
     mbar_init(done, 1);
-    *bad = 0;
+    *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     prefetch_map(&mapA);
     prefetch_map(&mapB);
@@ -174,102 +200,151 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  // stage s: A (hi in place) | A lo | B (hi in place) | B lo
-  auto tileA = [&](int s, int which) { return sm + s * TC_STAGE + which * TC_TILE_A; };
-  auto tileB = [&](int s, int which) { return sm + s * TC_STAGE + 2 * TC_TILE_A + which * TC_TILE_B; };
-  auto issue = [&](int kt, int s) {
-    mbar_expect_tx(&full[s], stage_bytes);
-    for (int r = 0; r < 128 / TC_BOX; ++r)
-      tma_load_3d(tileA(s, 0) + r * TC_BOX * TC_BK * 4, &mapA, kt * TC_BK, job.a_y + r * TC_BOX, job.a_z, &full[s]);
-    for (int r = 0; r < nb; ++r)
-      tma_load_3d(tileB(s, 0) + r * TC_BOX * TC_BK * 4, &mapB, kt * TC_BK, job.b_y + r * TC_BOX, 0, &full[s]);
+  // stage s: A | B (FP32 as loaded, hi in place after the split); the lo
+  // tiles of the step being multiplied after the ring: A lo | B lo
+  auto tileA = [&](int s) { return sm + s * TC_STAGE; };
+  auto tileB = [&](int s) { return sm + s * TC_STAGE + TC_TILE_A; };
+  unsigned char* loA = sm + TC_NST * TC_STAGE;
+  unsigned char* loB = loA + TC_TILE_A;
+  auto fail = [&]() {
+    *abort = 1;
+    atomicOr(err, 1u);
   };
-  int loads[2] = {0, 0};                            // thread 0's count of the loads issued per stage
-  if (tid == 0)
-    for (int kt = 0; kt < KT && kt < 2; ++kt) {
-      issue(kt, kt);
-      ++loads[kt];
-    }
-  const uint32_t idesc = tf32_idesc(job.nt);
-  int consumed = 0;                                 // K steps whose stage every thread has waited for
-  for (int kt = 0; kt < KT; ++kt) {
-    const int s = kt & 1;
-    const uint32_t ph = (uint32_t)(kt >> 1) & 1u;
-    const bool fail = !mbar_wait_bounded(&full[s], ph);
-    if (__syncthreads_or(fail || *bad)) {
-      if (tid == 0) *bad = 1;
-      break;
-    }
-    consumed = kt + 1;
-    {
-      float4* ah = reinterpret_cast<float4*>(tileA(s, 0));
-      float4* al = reinterpret_cast<float4*>(tileA(s, 1));
-      for (int i = tid; i < 128 * TC_BK / 4; i += TC_THREADS) tf32_split4(ah + i, al + i);
-      float4* bh = reinterpret_cast<float4*>(tileB(s, 0));
-      float4* bl = reinterpret_cast<float4*>(tileB(s, 1));
-      for (int i = tid; i < job.nt * TC_BK / 4; i += TC_THREADS) tf32_split4(bh + i, bl + i);
-    }
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a_hi = smem_addr(tileA(s, 0)), a_lo = smem_addr(tileA(s, 1));
-      const uint32_t b_hi = smem_addr(tileB(s, 0)), b_lo = smem_addr(tileB(s, 1));
-#pragma unroll
-      for (int k = 0; k < TC_BK / 8; ++k) {
-        // K = 8 TF32 per product: 32 bytes further along the swizzled row
-        const uint32_t off = (uint32_t)k * 32u;
-        const uint32_t acc0 = (kt > 0 || k > 0) ? 1u : 0u;
-        mma_tf32(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, acc0);
-        mma_tf32(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
-        mma_tf32(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
-      }
-      mma_commit(&empty[s]);
-      if (kt + 2 < KT) {
-        // the stage is free once these products have read it
-        if (mbar_wait_bounded(&empty[s], ph)) {
-          issue(kt + 2, s);
-          ++loads[s];
-        } else {
-          *bad = 1;                                 // seen by every thread at the next step
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA
+    if (lane == 0) {
+      int it = 0, issued[TC_NST] = {0, 0, 0};
+      for (int t = blockIdx.x; t < ntiles && !aborted(abort); t += gridDim.x) {
+        TcJob job = jobs[t / mtiles];
+        const int a_y = job.a_y + 128 * (t % mtiles);
+        const int nb = job.nt / TC_BOX;
+        const uint32_t bytes = (uint32_t)(128 / TC_BOX + nb) * TC_BOX * TC_BK * 4;
+        for (int kt = 0; kt < KT; ++kt, ++it) {
+          const int s = it % TC_NST, n = it / TC_NST;
+          if (!mbar_wait_bounded(&empty[s], (uint32_t)(n & 1) ^ 1u) || aborted(abort)) {
+            fail();
+            break;
+          }
+          mbar_expect_tx(&full[s], bytes);
+          for (int r = 0; r < 128 / TC_BOX; ++r)
+            tma_load_3d(tileA(s) + r * TC_BOX * TC_BK * 4, &mapA, kt * TC_BK, a_y + r * TC_BOX, job.a_z, &full[s]);
+          for (int r = 0; r < nb; ++r)
+            tma_load_3d(tileB(s) + r * TC_BOX * TC_BK * 4, &mapB, kt * TC_BK, job.b_y + r * TC_BOX, 0, &full[s]);
+          ++issued[s];
         }
       }
-    }
-  }
-  if (tid == 0) {
-    // the final commit covers every product issued
-    mma_commit(done);
-    if (*bad) {
-      // wait (bounded) for every load issued but not yet waited for before the CTA may exit
-      for (int kt = consumed; kt < consumed + 2 && kt < KT; ++kt) {
-        const int s = kt & 1;
-        if (loads[s] > (kt >> 1)) (void)mbar_wait_bounded(&full[s], (uint32_t)(kt >> 1) & 1u);
+      if (aborted(abort)) {
+        // every load issued must land before the CTA may exit
+        for (int s = 0; s < TC_NST; ++s)
+          if (issued[s] > 0) (void)mbar_wait_bounded(&full[s], (uint32_t)((issued[s] - 1) & 1));
       }
     }
-  }
-  if (!mbar_wait_bounded(done, 0)) atomicExch(bad, 1);
-  tc_fence_after();
-  __syncthreads();
-  const bool ok = *bad == 0;
-  float* S = reinterpret_cast<float*>(sm);
-  if (ok) {
-    // warp w reads lanes 32w..32w+31 of D: rows 32w + lane of the tile
-    const int row = warp * 32 + lane;
-    for (int c0 = 0; c0 < job.nt; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA
+    if (lane == 0) {
+      int it = 0, tc = 0;
+      for (int t = blockIdx.x; t < ntiles && !aborted(abort); t += gridDim.x, ++tc) {
+        TcJob job = jobs[t / mtiles];
+        const uint32_t idesc = tf32_idesc(job.nt);
+        const int a = tc & 1, u = tc >> 1;
+        if (!mbar_wait_bounded(&tempty[a], (uint32_t)(u & 1) ^ 1u)) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)(a * TC_MAXN);
+        bool ok = true;
+        for (int kt = 0; kt < KT; ++kt, ++it) {
+          const int s = it % TC_NST;
+          if (!mbar_wait_bounded(ready, (uint32_t)(it & 1)) || aborted(abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_hi = smem_addr(tileA(s)), a_lo = smem_addr(loA);
+          const uint32_t b_hi = smem_addr(tileB(s)), b_lo = smem_addr(loB);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) S[(c0 + i) * TC_LDS + row] = v[i];
+          for (int k = 0; k < TC_BK / 8; ++k) {
+            // K = 8 TF32 per product: 32 bytes further along the swizzled row
+            const uint32_t off = (uint32_t)k * 32u;
+            const uint32_t acc0 = (kt > 0 || k > 0) ? 1u : 0u;
+            mma_tf32(acc, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, acc0);
+            mma_tf32(acc, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+            mma_tf32(acc, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+          }
+          mma_commit(&empty[s]);
+          mma_commit(lofree);
+        }
+        if (!ok) {
+          fail();
+          break;
+        }
+        mma_commit(&tfull[a]);
+      }
+      // every product issued is complete before tensor memory is freed
+      mma_commit(done);
+      if (!mbar_wait_bounded(done, 0)) fail();
     }
-  } else if (tid == 0) {
-    atomicOr(err, 1u);
+  } else if (warp < 6) {
+    // -------------------------------------------------------------- split
+    const int st = tid - 64;                        // 0..127
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles && !aborted(abort); t += gridDim.x) {
+      const int nt = jobs[t / mtiles].nt;
+      bool ok = true;
+      for (int kt = 0; kt < KT; ++kt, ++it) {
+        const int s = it % TC_NST, n = it / TC_NST;
+        // the stage has landed, and the previous step's products no longer read the lo tiles
+        if (!mbar_wait_bounded(&full[s], (uint32_t)(n & 1)) ||
+            !mbar_wait_bounded(lofree, (uint32_t)(it & 1) ^ 1u) || aborted(abort)) {
+          ok = false;
+          break;
+        }
+        float4* ah = reinterpret_cast<float4*>(tileA(s));
+        float4* al = reinterpret_cast<float4*>(loA);
+#pragma unroll 4
+        for (int i = st; i < 128 * TC_BK / 4; i += 128) tf32_split4(ah + i, al + i);
+        float4* bh = reinterpret_cast<float4*>(tileB(s));
+        float4* bl = reinterpret_cast<float4*>(loB);
+#pragma unroll 4
+        for (int i = st; i < nt * TC_BK / 4; i += 128) tf32_split4(bh + i, bl + i);
+        fence_async_smem();
+        mbar_arrive(ready);
+      }
+      if (!ok) {
+        fail();
+        break;
+      }
+    }
+  } else {
+    // ----------------------------------------------------------- epilogue
+    const int lg = warp & 3;                        // tensor-memory lane group
+    const int row = lg * 32 + lane;                 // row of the 128-row tile
+    int tc = 0;
+    for (int t = blockIdx.x; t < ntiles && !aborted(abort); t += gridDim.x, ++tc) {
+      TcJob job = jobs[t / mtiles];
+      job.a_y += 128 * (t % mtiles);
+      const int a = tc & 1, u = tc >> 1;
+      if (!mbar_wait_bounded(&tfull[a], (uint32_t)(u & 1))) {
+        fail();
+        break;
+      }
+      tc_fence_after();
+      for (int c0 = 0; c0 < job.nt; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(a * TC_MAXN + c0), v);
+        epi.store16(job, row, c0, v, lane);
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[a]);
+    }
   }
   tc_fence_before();
   __syncthreads();
-  if (ok) epi.store(job, S, tid);
-  if (warp == 0) {
+  if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_MAXN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
   }
 }
 
@@ -314,7 +389,10 @@ static cudaError_t tc_launch(const CUtensorMap* maps, const TcJob* jobs, int njo
                              unsigned* err, cudaStream_t s) {
   static unsigned done = 0;
   set_smem_attr_once((const void*)tc_gemm_kernel<Epi>, TC_SMEM, &done);
-  tc_gemm_kernel<Epi><<<dim3(njobs, mtiles), TC_THREADS, TC_SMEM, s>>>(maps[0], maps[1], jobs, K, epi, err);
+  const int ntiles = njobs * mtiles;
+  const int sms = current_sm_count();
+  const int grid = ntiles < sms ? ntiles : sms;
+  tc_gemm_kernel<Epi><<<grid, TC_THREADS, TC_SMEM, s>>>(maps[0], maps[1], jobs, ntiles, mtiles, K, epi, err);
   return cudaGetLastError();
 }
 
@@ -326,20 +404,25 @@ struct EpiLegendre {
   double* coeffs;
   int N, rows;            // rows of D that exist: 2 B
   size_t ncoef;
-  // thread t takes (set, column) pairs with the column fastest: a set's
-  // coefficients of one order and parity lie 32 bytes apart
-  __device__ void store(const TcJob& j, const float* S, int tid) const {
+  // row: the thread's row of the tile (tensor-memory lane), with the
+  // imaginary part of its set in the neighbouring lane (row + 1); the even
+  // lane writes the 16 complex coefficients of its set for columns c0 ...
+  __device__ void store16(const TcJob& j, int row, int c0, const float* v, int lane) const {
+    float w[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) w[i] = __shfl_xor_sync(0xffffffffu, v[i], 1);
+    const int r = j.a_y + row;
+    if ((lane & 1) || r >= rows) return;
     const int m = j.e0;
     const size_t row0 = (size_t)m * (N + 1) - (size_t)m * (m - 1) / 2;
-    const int sets = 64;                           // 128 rows of D: 64 sets
-    for (int idx = tid; idx < sets * j.nt; idx += TC_THREADS) {
-      const int bl = idx / j.nt, c = idx - bl * j.nt;
-      const int r = j.a_y + 2 * bl;
-      const int jj = j.e2 + c;
-      if (r >= rows || jj >= j.e3) continue;
-      const int l = m + j.e1 + 2 * jj;
-      double2* out = reinterpret_cast<double2*>(coeffs) + (size_t)(r >> 1) * ncoef + row0 + (size_t)(l - m);
-      *out = make_double2((double)S[c * TC_LDS + 2 * bl], (double)S[c * TC_LDS + 2 * bl + 1]);
+    double2* out = reinterpret_cast<double2*>(coeffs) + (size_t)(r >> 1) * ncoef + row0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int jj = j.e2 + c0 + i;
+      if (c0 + i < j.nt && jj < j.e3) {
+        const int l = m + j.e1 + 2 * jj;
+        out[l - m] = make_double2((double)v[i], (double)w[i]);
+      }
     }
   }
 };
@@ -393,11 +476,13 @@ cudaError_t tc_legendre(const GridTables& g, const float* G, int B, const TcJob*
 struct EpiDense {
   float* C;
   int M, N, ldc;
-  __device__ void store(const TcJob& j, const float* S, int tid) const {
-    for (int idx = tid; idx < 128 * j.nt; idx += TC_THREADS) {
-      const int row = idx / j.nt, c = idx - row * j.nt;
-      const int r = j.a_y + row, cc = j.b_y + c;
-      if (r < M && cc < N) C[(size_t)r * ldc + cc] = S[c * TC_LDS + row];
+  __device__ void store16(const TcJob& j, int row, int c0, const float* v, int) const {
+    const int r = j.a_y + row;
+    if (r >= M) return;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int cc = j.b_y + c0 + i;
+      if (cc < N) C[(size_t)r * ldc + cc] = v[i];
     }
   }
 };
