@@ -8,7 +8,8 @@
 * a batch captured in one CUDA graph equals its fits run alone, replayed
   twice on plans that ran other fits before the capture;
 * a fit with a non-finite value reports its own status in the batch while
-  the fits around it (on the same plan) report none.
+  the fits around it (on the same plan) report none;
+* the FP64 form of a batch matches the oracle's fits to 1e-10 on a subset.
 """
 import dataclasses
 
@@ -125,4 +126,22 @@ def test_batch_equals_alone_and_reports_per_fit_status(h, graph):
     for i in range(len(specs)):
         if i != bad:
             assert torch.equal(res.outputs[i], alone[i])
+    pool.close()
+
+
+def test_batch_fp64_matches_oracle(h):
+    """A batch in the FP64 form (plans reused across fits of different node
+    counts on two slots) against the oracle's whole fits."""
+    import oracle as O
+    from paper_2609_39200_b300.batch import PlanPool, run_batch
+    specs = [_spec(60 + i, N, K, M, holes=holes) for i, (N, K, M, holes) in enumerate(
+        [(16, 2, 4000, (10.0,)), (16, 3, 6000, ()), (32, 2, 5000, (20.0,)), (16, 2, 3000, ())])]
+    pool = PlanPool(device=torch.device("cuda"), min_capacity=1 << 13)
+    res = run_batch(specs, _load, pool, n_slots=2, precision="fp64", device=torch.device("cuda"))
+    assert res.status == [0] * len(specs)
+    for i, s in enumerate(specs):
+        x, y = _load(s)
+        r = O.hamls(x.cpu().numpy(), y.cpu().numpy(), s.N, s.K, O.Params())
+        got = h.to_complex(res.outputs[i])
+        assert np.linalg.norm(got - r.coeffs) / np.linalg.norm(r.coeffs) < 1e-10, f"fit {i} (N={s.N}, M={s.M})"
     pool.close()
