@@ -59,11 +59,13 @@ __global__ void __launch_bounds__(256) ring_fft_kernel(const double* __restrict_
     const int T_ = L / R;
     const int NsR = Ns * R;
     const int strideA = L / NsR, strideB = L / R;
-    if (R <= 32) {
-      // one butterfly per thread: group g = (hi, jl) reads in[j + q T_] for
+    if (R <= 32 && T_ >= (int)blockDim.x) {
+      // one butterfly per thread (while there are at least as many
+      // butterflies as threads): group g = (hi, jl) reads in[j + q T_] for
       // q < R and writes out[hi Ns R + jl + r Ns] for r < R (one division per
       // group); twiddle exponents q (jl strideA + r strideB) advance by
-      // additions mod L
+      // additions mod L. A large radix with few butterflies (19 for
+      // L = 1026: 54 of them) takes the one-output-per-thread form below.
       for (int g = threadIdx.x; g < T_; g += blockDim.x) {
         const int hi = g / Ns, jl = g - hi * Ns;
         const int j = hi * Ns + jl;
