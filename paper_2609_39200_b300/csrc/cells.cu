@@ -2,6 +2,8 @@
 // a stable LSD radix sort of (key, index), the CSR run table and the sorted
 // FP64/FP32 copies of the points. Everything is bit-exact integer work or
 // exact copies; see common.cuh for the key definition.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -248,39 +250,6 @@ __global__ void csr_kernel(const uint32_t* __restrict__ sk, int n, int ncells, u
 }
 
 // --------------------------------------------------------------- staging
-__global__ void stage_points_kernel(const double* __restrict__ xyz, const uint32_t* __restrict__ perm, int n,
-                                    double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz,
-                                    float4* __restrict__ pf, const double* __restrict__ wts,
-                                    double* __restrict__ sw, float* __restrict__ swf) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  size_t o = perm[i];
-  double x = xyz[3 * o], y = xyz[3 * o + 1], z = xyz[3 * o + 2];
-  px[i] = x;
-  py[i] = y;
-  pz[i] = z;
-  pf[i] = make_float4((float)x, (float)y, (float)z, 0.f);
-  if (wts) {
-    double w = wts[o];
-    sw[i] = w;
-    swf[i] = (float)w;
-  }
-}
-
-__global__ void stage_soa_kernel(const double* __restrict__ ax, const double* __restrict__ ay,
-                                 const double* __restrict__ az, const uint32_t* __restrict__ perm, int n,
-                                 double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz,
-                                 float4* __restrict__ pf) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t o = perm[i];
-  double x = ax[o], y = ay[o], z = az[o];
-  px[i] = x;
-  py[i] = y;
-  pz[i] = z;
-  pf[i] = make_float4((float)x, (float)y, (float)z, 0.f);
-}
-
 // per fit: values into sorted order (FP64 and the FP32 slot of pf)
 __global__ void stage_values_kernel(const double* __restrict__ y, const uint32_t* __restrict__ perm, int n,
                                     double* __restrict__ sy, float4* __restrict__ pf, int write64, DevStatus* st) {
@@ -295,29 +264,162 @@ __global__ void stage_values_kernel(const double* __restrict__ y, const uint32_t
   pf[i].w = (float)v;
 }
 
+// ------------------------------------------------- counting sort by cell
+// A cell holds a few points, so the points are sorted by counting: each
+// takes an arrival rank in its cell (an atomic on the cell's count), the
+// counts are scanned into the CSR start table, each point scatters to
+// start + rank, and a last pass orders every cell's points by input index
+// (the order a stable sort gives, whatever order the atomics ran in) while
+// writing the sorted FP64/FP32 copies.
+//
+// The key of a point comes from FP32 arithmetic where that is provably the
+// FP64 key (cell_key_fast); the rest (about one point in a hundred) are
+// listed and keyed in FP64 by a second kernel, so no warp of the first
+// waits on the slow FP64 pipe for one lane.
+__device__ __forceinline__ void load_point(const double* __restrict__ xyz, const double* __restrict__ ax,
+                                           const double* __restrict__ ay, const double* __restrict__ az, size_t i,
+                                           double& x, double& y, double& z) {
+  if (xyz) {
+    x = xyz[3 * i];
+    y = xyz[3 * i + 1];
+    z = xyz[3 * i + 2];
+  } else {
+    x = ax[i];
+    y = ay[i];
+    z = az[i];
+  }
+}
+
+__global__ void cell_count_kernel(const double* __restrict__ xyz, const double* __restrict__ ax,
+                                  const double* __restrict__ ay, const double* __restrict__ az, int n, int B, int P,
+                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ rank,
+                                  uint32_t* __restrict__ count, uint32_t* __restrict__ slow,
+                                  uint32_t* __restrict__ nslow, DevStatus* st) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool act = i < n;
+  bool fast = true;
+  if (act) {
+    double x, y, z;
+    load_point(xyz, ax, ay, az, (size_t)i, x, y, z);
+    const float xf = (float)x, yf = (float)y, zf = (float)z;
+    bool ok = true;
+    if (xyz) {
+      // unit-vector check in FP32 where it is certain (the FP32 |x|^2 is
+      // within 4e-7 of the exact one), in FP64 otherwise
+      const float r2f = xf * xf + yf * yf + zf * zf;
+      ok = isfinite(r2f) && fabsf(r2f - 1.f) < 5e-7f;
+      if (!ok) {
+        const double r2 = x * x + y * y + z * z;
+        ok = isfinite(x) && isfinite(y) && isfinite(z) && fabs(r2 - 1.0) < 1e-6;
+      }
+    }
+    uint32_t key = 0;
+    if (!ok) {
+      set_flag(st, ST_BADNODE);
+      key = cell_key64(0.0, 0.0, 1.0, B, P);
+    } else {
+      fast = cell_key_fast(xf, yf, zf, (float)__dsub_rn(1.0, fabs(z)), B, P, key);
+    }
+    if (fast) {
+      keys[i] = key;
+      rank[i] = atomicAdd(&count[key], 1u);
+    }
+  }
+  const unsigned bal = __ballot_sync(FULL, act && !fast);
+  if (bal) {
+    const int leader = __ffs(bal) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(nslow, (uint32_t)__popc(bal));
+    base = __shfl_sync(FULL, base, leader);
+    if (act && !fast) slow[base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
+  }
+}
+
+__global__ void cell_count_slow_kernel(const double* __restrict__ xyz, const double* __restrict__ ax,
+                                       const double* __restrict__ ay, const double* __restrict__ az, int B, int P,
+                                       const uint32_t* __restrict__ slow, const uint32_t* __restrict__ nslow,
+                                       uint32_t* __restrict__ keys, uint32_t* __restrict__ rank,
+                                       uint32_t* __restrict__ count) {
+  const uint32_t ns = *nslow;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ns; t += gridDim.x * blockDim.x) {
+    const uint32_t i = slow[t];
+    double x, y, z;
+    load_point(xyz, ax, ay, az, i, x, y, z);
+    const uint32_t key = cell_key64(x, y, z, B, P);
+    keys[i] = key;
+    rank[i] = atomicAdd(&count[key], 1u);
+  }
+}
+
+__global__ void cell_scatter_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ rank,
+                                    const uint32_t* __restrict__ start, int n, uint32_t* __restrict__ tmp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  tmp[start[keys[i]] + rank[i]] = (uint32_t)i;
+}
+
+// tmp holds every cell's points in arrival order; a point's place in its
+// cell is the number of the cell's points with a smaller input index
+__global__ void cell_order_kernel(const uint32_t* __restrict__ tmp, const uint32_t* __restrict__ keys,
+                                  const uint32_t* __restrict__ start, int n, const double* __restrict__ xyz,
+                                  const double* __restrict__ ax, const double* __restrict__ ay,
+                                  const double* __restrict__ az, const double* __restrict__ wts,
+                                  uint32_t* __restrict__ perm, uint32_t* __restrict__ skeys, double* __restrict__ px,
+                                  double* __restrict__ py, double* __restrict__ pz, float4* __restrict__ pf,
+                                  double* __restrict__ sw, float* __restrict__ swf) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const uint32_t i = tmp[j];
+  const uint32_t key = keys[i];
+  const uint32_t c0 = start[key], c1 = start[key + 1];
+  uint32_t r = 0;
+  for (uint32_t m = c0; m < c1; ++m) r += tmp[m] < i ? 1u : 0u;
+  const uint32_t p = c0 + r;
+  perm[p] = i;
+  skeys[p] = key;
+  double x, y, z;
+  load_point(xyz, ax, ay, az, i, x, y, z);
+  px[p] = x;
+  py[p] = y;
+  pz[p] = z;
+  pf[p] = make_float4((float)x, (float)y, (float)z, 0.f);
+  if (wts) {
+    const double w = wts[i];
+    sw[p] = w;
+    swf[p] = (float)w;
+  }
+}
+
 void build_cells(const CellBuild& cb, cudaStream_t s, int64_t* launches) {
   const int n = cb.n;
   const int T = 256;
   const int gb = (n + T - 1) / T;
-  if (cb.xyz_aos)
-    keys_kernel<<<gb, T, 0, s>>>(cb.xyz_aos, n, cb.B, cb.P, cb.keys, cb.vals, cb.st);
-  else
-    keys_kernel_soa<<<gb, T, 0, s>>>(cb.ax, cb.ay, cb.az, n, cb.B, cb.P, cb.keys, cb.vals);
-  ++*launches;
-  int bits = 0;
-  while ((1u << bits) < (uint32_t)(cb.B * cb.P)) ++bits;
-  bool alt = radix_sort_pairs(cb.keys, cb.vals, cb.keys_alt, cb.vals_alt, n, bits, cb.counts, s, launches);
-  const uint32_t* sk = alt ? cb.keys_alt : cb.keys;
-  const uint32_t* perm = alt ? cb.vals_alt : cb.vals;
-  csr_kernel<<<(n + 1 + T - 1) / T, T, 0, s>>>(sk, n, cb.B * cb.P, cb.start);
-  ++*launches;
-  if (cb.xyz_aos)
-    stage_points_kernel<<<gb, T, 0, s>>>(cb.xyz_aos, perm, n, cb.px, cb.py, cb.pz, cb.pf, cb.wts, cb.sw, cb.swf);
-  else
-    stage_soa_kernel<<<gb, T, 0, s>>>(cb.ax, cb.ay, cb.az, perm, n, cb.px, cb.py, cb.pz, cb.pf);
-  ++*launches;
-  *cb.perm_out = perm;
-  *cb.keys_out = sk;
+  const int ncells = cb.B * cb.P;
+  uint32_t* nslow = cb.counts;               // one word
+  uint32_t* part = cb.counts + 4;            // scan scratch
+  const double* xyz = cb.xyz_aos;
+  cudaMemsetAsync(cb.start, 0, ((size_t)ncells + 1) * sizeof(uint32_t), s);
+  cudaMemsetAsync(nslow, 0, sizeof(uint32_t), s);
+  if (n > 0) {
+    cell_count_kernel<<<gb, T, 0, s>>>(xyz, cb.ax, cb.ay, cb.az, n, cb.B, cb.P, cb.keys, cb.vals, cb.start,
+                                       cb.keys_alt, nslow, cb.st);
+    cell_count_slow_kernel<<<std::min(gb, 128), T, 0, s>>>(xyz, cb.ax, cb.ay, cb.az, cb.B, cb.P, cb.keys_alt,
+                                                           nslow, cb.keys, cb.vals, cb.start);
+    *launches += 2;
+  }
+  exclusive_scan_u32(cb.start, ncells + 1, part, s, launches);
+  if (n > 0) {
+    // the arrival ranks (vals) and the slow list (keys_alt) are spent: the
+    // scatter reuses keys_alt, the sorted keys go to vals
+    cell_scatter_kernel<<<gb, T, 0, s>>>(cb.keys, cb.vals, cb.start, n, cb.keys_alt);
+    cell_order_kernel<<<gb, T, 0, s>>>(cb.keys_alt, cb.keys, cb.start, n, xyz, cb.ax, cb.ay, cb.az,
+                                       xyz ? cb.wts : nullptr, cb.vals_alt, cb.vals, cb.px, cb.py, cb.pz, cb.pf,
+                                       cb.sw, cb.swf);
+    *launches += 2;
+  }
+  *cb.perm_out = cb.vals_alt;
+  *cb.keys_out = cb.vals;
 }
 
 // A second ordering of already sorted points by a coarser band structure:
