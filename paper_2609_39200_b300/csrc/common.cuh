@@ -420,6 +420,24 @@ __device__ __forceinline__ T weight_phi(int fn, T r) {
 __device__ __forceinline__ double geodesic_from_chord2(double c2) { return 2.0 * asin(0.5 * sqrt(c2)); }
 __device__ __forceinline__ float geodesic_from_chord2(float c2) { return 2.f * asinf(0.5f * sqrtf(c2)); }
 
+// The same in FP32 by the Maclaurin series of arcsin,
+//   asin(s) = sum_k (2k)! / (4^k (k!)^2 (2k + 1)) s^(2k+1),
+// through s^11 where s = sqrt(c2)/2 <= 1/4 (the first omitted term is below
+// 1.1e-9 of the sum there, far below FP32 rounding), asinf beyond: the MLS
+// weights of supports up to about 29 degrees without the general routine.
+__device__ __forceinline__ float geodesic_series_f(float c2) {
+  const float s = 0.5f * sqrtf(c2);
+  if (s > 0.25f) return 2.f * asinf(s);
+  const float t = s * s;
+  float p = 63.f / 2816.f;
+  p = __fmaf_rn(p, t, 35.f / 1152.f);
+  p = __fmaf_rn(p, t, 5.f / 112.f);
+  p = __fmaf_rn(p, t, 3.f / 40.f);
+  p = __fmaf_rn(p, t, 1.f / 6.f);
+  p = __fmaf_rn(p, t, 1.f);
+  return 2.f * s * p;
+}
+
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;
   x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;

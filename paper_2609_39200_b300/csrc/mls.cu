@@ -190,29 +190,32 @@ __device__ __forceinline__ S solve_local(const S* mw, const S* my, const SolvePa
 
 template <typename T, int K>
 __device__ __forceinline__ void accumulate(T (&acc)[Shape<K>::NV], T w, T u, T v, T y) {
+  // w u^a and v^b once, then one fused multiply-add per moment
   constexpr int D2 = 2 * K, D1 = K, NM = Shape<K>::NM;
-  T vb = w;
+  T wu[D2 + 1], vp[D2 + 1];
+  wu[0] = w;
+  vp[0] = T(1);
+  vp[1] = v;
 #pragma unroll
-  for (int b = 0; b <= D2; ++b) {
-    T t = vb;
+  for (int e = 1; e <= D2; ++e) wu[e] = wu[e - 1] * u;
 #pragma unroll
-    for (int a = 0; a <= D2 - b; ++a) {
-      acc[midx(a, b, D2)] += t;
-      if (a < D2 - b) t *= u;
-    }
-    if (b < D2) vb *= v;
-  }
-  T vy = w * y;
+  for (int e = 2; e <= D2; ++e) vp[e] = vp[e - 1] * v;
 #pragma unroll
-  for (int b = 0; b <= D1; ++b) {
-    T t = vy;
+  for (int a = 0; a <= D2; ++a) acc[midx(a, 0, D2)] += wu[a];
 #pragma unroll
-    for (int a = 0; a <= D1 - b; ++a) {
-      acc[NM + midx(a, b, D1)] += t;
-      if (a < D1 - b) t *= u;
-    }
-    if (b < D1) vy *= v;
-  }
+  for (int b = 1; b <= D2; ++b)
+#pragma unroll
+    for (int a = 0; a <= D2 - b; ++a) acc[midx(a, b, D2)] = fma(wu[a], vp[b], acc[midx(a, b, D2)]);
+  T wyu[D1 + 1];
+  wyu[0] = w * y;
+#pragma unroll
+  for (int e = 1; e <= D1; ++e) wyu[e] = wyu[e - 1] * u;
+#pragma unroll
+  for (int a = 0; a <= D1; ++a) acc[NM + midx(a, 0, D1)] += wyu[a];
+#pragma unroll
+  for (int b = 1; b <= D1; ++b)
+#pragma unroll
+    for (int a = 0; a <= D1 - b; ++a) acc[NM + midx(a, b, D1)] = fma(wyu[a], vp[b], acc[NM + midx(a, b, D1)]);
 }
 
 // The value weights of the local problem. For fixed nodes the Gram moments,
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(MLS_WARPS * 32, 7) mls_gather_kernel(MlsArgs a
           const float c2 = dx * dx + dy * dy + dz * dz;
           if (!(c2 < r2f)) return;
           ++nin;
-          float w = weight_phi(a.weight_fn, geodesic_from_chord2(c2) * idf);
+          float w = weight_phi(a.weight_fn, geodesic_series_f(c2) * idf);
           if (a.swf) w *= a.swf[idx];
           const float u = e1x * dx + e1y * dy + e1z * dz;
           const float v = e2x * dx + e2y * dy;
@@ -667,7 +670,7 @@ __global__ void __launch_bounds__(128) op_rows_kernel(MlsArgs a, const double* _
           const float c2 = dx * dx + dy * dy + dz * dz;
           in = c2 < r2f;
           if (in && FILL) {
-            w = weight_phi(a.weight_fn, geodesic_from_chord2(c2) * idf);
+            w = weight_phi(a.weight_fn, geodesic_series_f(c2) * idf);
             if (a.swf) w *= a.swf[idx];
             u = e1x * dx + e1y * dy + e1z * dz;
             v = e2x * dx + e2y * dy;
