@@ -2,7 +2,7 @@
 """Benchmark of the HAMLS hot path on S^2: fits/s at N=512, K=3, M=4,000,000.
 
 One step = one whole fit of one synthetic input: the node-dependent plan
-stage (cell keys, radix sort, runs, auxiliary k-NN, Shepard support radius,
+stage (cell keys, counting sort by cell, runs, auxiliary k-NN, Shepard support radius,
 work ordering; hamls_replan) and the value-dependent stage (value staging,
 MLS with n(q) at all 526,338 grid nodes, ring FFT, Legendre quadrature;
 hamls_fit). Inputs are resident in device memory when a step starts; a
@@ -872,10 +872,12 @@ def run_ours(args):
     while B_cells * B_cells * 4 < w.M and B_cells < 4096:
         B_cells *= 2
     alg = {
-        # per node: xyz in (24 B), key and index out (8 B), three radix passes over (key, index) (16 B
-        # each), staging xyz in (24 B) and the FP64 + FP32 copies out (40 B); the CSR run table
-        "cells": ("keys_kernel + radix sort + csr_kernel + stage_points_kernel",
-                  w.M * (24 + 8 + 3 * 16 + 24 + 40) + 4 * (B_cells * 2 * B_cells + 1)),
+        # per node: keys pass xyz in (24 B), key and arrival rank out (8 B); scatter key and rank in
+        # (8 B), position out (4 B); ordering pass position and key in (8 B), xyz in (24 B), order and
+        # sorted key out (8 B), FP64 + FP32 copies out (40 B). Per cell: count cleared, scanned in
+        # place (12 B)
+        "cells": ("cell_count_kernel + cell_scatter_kernel + cell_order_kernel (+ scan of the counts)",
+                  w.M * (24 + 8 + 8 + 4 + 8 + 24 + 8 + 40) + 12 * (B_cells * 2 * B_cells + 1)),
         # n nearest FP32 node records (x, y, z, y) per auxiliary point + its FP64 coordinates + d_n out
         "aux_knn": ("aux_knn_kernel", stats["aux_points"] * (16 * n_nb + 24 + 8)),
         # gathered FP32 node records + per grid node delta, rho2 (in), f (out), order key
