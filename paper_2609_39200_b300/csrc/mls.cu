@@ -325,36 +325,55 @@ __device__ void solve_gamma(const double* mw, const SolveParams& P, double* gamm
 
 constexpr int MLS_WARPS = 4;
 
-// Warp reduce-scatter of up to 64 per-lane partial sums: five exchange steps
-// halve the set each lane carries (62 shuffles instead of 5 NV), after which
-// lane l holds the totals of entries 2l and 2l+1.
+// Warp reduce-scatter of NV <= 64 per-lane partial sums: five exchange steps
+// (partner lane ^ 16, 8, 4, 2, 1), each halving, rounded up, the set a lane
+// carries: a lane with the step's bit keeps the upper half and sends the
+// lower one, the other the reverse, one shuffle per kept entry (38 -> 19 ->
+// 10 -> 5 -> 3 -> 2 at K = 3: 39 shuffles). Afterwards each lane holds the
+// totals of at most two entries; idx gives their original indices (-1 for a
+// padding slot).
+template <typename T, int S, int O, int H = (S + 1) / 2>
+__device__ __forceinline__ void rs_step(const T (&in)[S], T (&out)[H], int lane) {
+  const bool b = lane & O;
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    const T lo = in[i];
+    const T hi = (H + i < S) ? in[(H + i < S) ? H + i : 0] : T(0);
+    out[i] = (b ? hi : lo) + __shfl_xor_sync(FULL, b ? lo : hi, O);
+  }
+}
+
+template <int S, int O>
+__device__ __forceinline__ void rs_index(int lane, int& j, bool& valid) {
+  constexpr int H = (S + 1) / 2;
+  j = (lane & O) ? H + j : j;
+  valid = valid && j < S;
+}
+
 template <typename T, int NV>
-__device__ __forceinline__ void reduce_scatter64(const T (&acc)[NV], T& out0, T& out1) {
+__device__ __forceinline__ void reduce_scatter(const T (&acc)[NV], T (&out)[2], int (&idx)[2]) {
   static_assert(NV <= 64, "at most 64 moments");
+  constexpr int S1 = NV, S2 = (S1 + 1) / 2, S3 = (S2 + 1) / 2, S4 = (S3 + 1) / 2, S5 = (S4 + 1) / 2;
+  constexpr int S6 = (S5 + 1) / 2;
   const int lane = threadIdx.x & 31;
-  T v[32];
-  {
-    const bool b = lane & 16;
+  T v2[S2], v3[S3], v4[S4], v5[S5], v6[S6];
+  rs_step<T, S1, 16>(acc, v2, lane);
+  rs_step<T, S2, 8>(v2, v3, lane);
+  rs_step<T, S3, 4>(v3, v4, lane);
+  rs_step<T, S4, 2>(v4, v5, lane);
+  rs_step<T, S5, 1>(v5, v6, lane);
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      const T lo = i < NV ? acc[i] : T(0);
-      const T hi = (i + 32) < NV ? acc[(i + 32) < NV ? i + 32 : 0] : T(0);
-      v[i] = (b ? hi : lo) + __shfl_xor_sync(FULL, b ? lo : hi, 16);
-    }
+  for (int i = 0; i < 2; ++i) {
+    int j = i;
+    bool valid = i < S6;
+    rs_index<S5, 1>(lane, j, valid);
+    rs_index<S4, 2>(lane, j, valid);
+    rs_index<S3, 4>(lane, j, valid);
+    rs_index<S2, 8>(lane, j, valid);
+    rs_index<S1, 16>(lane, j, valid);
+    out[i] = i < S6 ? v6[i < S6 ? i : 0] : T(0);
+    idx[i] = valid ? j : -1;
   }
-#pragma unroll
-  for (int w = 16, o = 8; w >= 2; w >>= 1, o >>= 1) {
-    const bool b = lane & o;
-#pragma unroll
-    for (int i = 0; i < w; ++i) {
-      if (i < w) {
-        const T lo = v[i], hi = v[i + w];
-        v[i] = (b ? hi : lo) + __shfl_xor_sync(FULL, b ? lo : hi, o);
-      }
-    }
-  }
-  out0 = v[0];
-  out1 = v[1];
 }
 
 // Gather: one warp per grid node (heaviest first; the `heavy` first nodes of
@@ -448,11 +467,12 @@ __global__ void __launch_bounds__(MLS_WARPS * 32, 7) mls_gather_kernel(MlsArgs a
           accumulate<T, K>(acc, (T)w, (T)u, (T)v, (T)a.sy[idx]);
         });
       }
-      T o0, o1;
-      reduce_scatter64<T, NV>(acc, o0, o1);
+      T o[2];
+      int oi[2];
+      reduce_scatter<T, NV>(acc, o, oi);
       T* dst = mom + pos * NVP;
-      if (2 * lane < NV) dst[2 * lane] = o0;
-      if (2 * lane + 1 < NV) dst[2 * lane + 1] = o1;
+      if (oi[0] >= 0) dst[oi[0]] = o[0];
+      if (oi[1] >= 0) dst[oi[1]] = o[1];
       if (!LIST) {
         nin = warp_sum(nin);
         if (lane == 0) {
