@@ -106,8 +106,11 @@ __device__ __forceinline__ S solve_local(const S* mw, const S* my, const SolvePa
     zv[j] = my[midx(ea_of(j + 1), eb_of(j + 1), D1)] * is[j + 1] * isW;
   }
   const S beta = my[0] / W;
-  // Cholesky with the pivot floor
+  // Cholesky with the pivot floor. In FP64 (slow square roots and
+  // divisions on this pipe) 1/l_jj is one reciprocal square root, l_jj
+  // = s_jj / sqrt(s_jj) one product, and the substitutions reuse 1/l_jj.
   bool drop[mm];
+  S invd[mm];
   minpiv = S(1);
   ndrop = 0;
 #pragma unroll
@@ -118,8 +121,15 @@ __device__ __forceinline__ S solve_local(const S* mw, const S* my, const SolvePa
     drop[j] = !(sjj > S(P.floor_));
     ndrop += drop[j] ? 1 : 0;
     minpiv = sjj < minpiv ? sjj : minpiv;
-    const S ljj = drop[j] ? S(0) : sqrt(sjj);
-    const S inv = drop[j] ? S(0) : S(1) / ljj;
+    S ljj, inv;
+    if (sizeof(S) == 8) {
+      inv = drop[j] ? S(0) : rsqrt_t<S>(sjj);
+      ljj = sjj * inv;
+    } else {
+      ljj = drop[j] ? S(0) : sqrt(sjj);
+      inv = drop[j] ? S(0) : S(1) / ljj;
+    }
+    invd[j] = inv;
     L[tri(j, j)] = ljj;
 #pragma unroll
     for (int i = j + 1; i < mm; ++i) {
@@ -142,7 +152,7 @@ __device__ __forceinline__ S solve_local(const S* mw, const S* my, const SolvePa
       vb -= L[tri(j, k)] * d[k];
       vz -= L[tri(j, k)] * e[k];
     }
-    const S inv = drop[j] ? S(0) : S(1) / L[tri(j, j)];
+    const S inv = (sizeof(S) == 8) ? invd[j] : (drop[j] ? S(0) : S(1) / L[tri(j, j)]);
     d[j] = vb * inv;
     e[j] = vz * inv;
     Dl[deg_of(j + 1)] += d[j] * d[j];
@@ -249,24 +259,25 @@ __device__ void solve_gamma(const double* mw, const SolveParams& P, double* gamm
 #pragma unroll
   for (int j = 0; j < mm; ++j) bv[j] = mw[midx(ea_of(j + 1), eb_of(j + 1), D2)] * is[j + 1] * isW;
   bool drop[mm];
+  S inv[mm];
 #pragma unroll
   for (int j = 0; j < mm; ++j) {
     S sjj = L[tri(j, j)];
 #pragma unroll
     for (int k = 0; k < j; ++k) sjj -= L[tri(j, k)] * L[tri(j, k)];
     drop[j] = !(sjj > S(P.floor_));
-    const S ljj = drop[j] ? S(0) : sqrt(sjj);
-    const S inv = drop[j] ? S(0) : S(1) / ljj;
-    L[tri(j, j)] = ljj;
+    // as solve_local's FP64 form: 1/l_jj by one reciprocal square root
+    inv[j] = drop[j] ? S(0) : rsqrt_t<S>(sjj);
+    L[tri(j, j)] = sjj * inv[j];
 #pragma unroll
     for (int i = j + 1; i < mm; ++i) {
       S v = L[tri(i, j)];
 #pragma unroll
       for (int k = 0; k < j; ++k) v -= L[tri(i, k)] * L[tri(j, k)];
-      L[tri(i, j)] = v * inv;
+      L[tri(i, j)] = v * inv[j];
     }
   }
-  S d[mm], inv[mm];
+  S d[mm];
   S Dl[K + 1];
 #pragma unroll
   for (int l = 0; l <= K; ++l) Dl[l] = S(0);
@@ -275,7 +286,6 @@ __device__ void solve_gamma(const double* mw, const SolveParams& P, double* gamm
     S vb = bv[j];
 #pragma unroll
     for (int k = 0; k < j; ++k) vb -= L[tri(j, k)] * d[k];
-    inv[j] = drop[j] ? S(0) : S(1) / L[tri(j, j)];
     d[j] = vb * inv[j];
     Dl[deg_of(j + 1)] += d[j] * d[j];
   }
