@@ -62,11 +62,12 @@ __global__ void reset_status_kernel(DevStatus* st, int full) {
     if (full) {
       st->flags = 0;
       st->tc_err = 0;
-      for (int i = 0; i < 16; ++i) st->cnt[i] = 0;
+      for (int i = 0; i < C_NCOUNT; ++i) st->cnt[i] = 0;
       st->cnt[C_MIN_N] = ~0ull;
     } else {
       // per fit: the gather recounts n(q) and re-runs the guard
       st->cnt[C_REG] = st->cnt[C_REDO] = st->cnt[C_DROP] = st->cnt[C_BATCH] = st->cnt[C_REDO_LIST] = 0;
+      st->cnt[C_REG_LIST] = 0;
       st->cnt[C_SUM_N] = st->cnt[C_MAX_N] = st->cnt[C_GUARD] = st->cnt[C_GUARD_LIST] = st->cnt[C_LIST_BATCH] = 0;
       st->cnt[C_MIN_N] = ~0ull;
     }
@@ -137,6 +138,7 @@ struct hamls_plan_s {
   double *delta, *rho2, *fgrid, *chi, *tau;
   float *deltaf, *rho2f;
   uint32_t* redo_list;
+  uint32_t* reg_list;
   int32_t* count;
   uint8_t* guarded;
   uint32_t *guard_list, *okeys, *ovals, *okeys_alt, *ovals_alt;
@@ -231,6 +233,7 @@ void carve(hamls_plan_s* P) {
   P->deltaf = A.take<float>(MQ);
   P->rho2f = A.take<float>(MQ);
   P->redo_list = A.take<uint32_t>(MQ);
+  P->reg_list = A.take<uint32_t>(MQ);
   P->fgrid = A.take<double>(MQ);
   P->chi = A.take<double>(MQ);
   P->tau = A.take<double>(MQ);
@@ -700,6 +703,7 @@ static MlsArgs mls_args(hamls_plan_s* P) {
   for (int l = 0; l <= KMAX; ++l) a.mu[l] = pow((double)l * (l + 1), P->p.sobolev_s);
   a.mom = P->mom;
   a.redo_list = P->redo_list;
+  a.reg_list = P->reg_list;
   a.m = P->m;
   a.count = P->count;
   a.guarded = P->guarded;

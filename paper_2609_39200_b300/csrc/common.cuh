@@ -35,12 +35,12 @@ enum : unsigned {
 
 // device counters
 enum { C_SUM_N = 0, C_MIN_N, C_MAX_N, C_REG, C_GUARD, C_REDO, C_DROP, C_GUARD_LIST, C_REDO_LIST,
-       C_BATCH, C_TILE, C_KNN_CAND, C_KNN_SCAN, C_KNN_EXACT_FB, C_LIST_BATCH, C_OP_TOTAL, C_NCOUNT };
+       C_BATCH, C_TILE, C_KNN_CAND, C_KNN_SCAN, C_KNN_EXACT_FB, C_LIST_BATCH, C_OP_TOTAL, C_REG_LIST, C_NCOUNT };
 
 struct DevStatus {
   unsigned flags;
   unsigned tc_err;          // tensor-core tiles that gave up waiting (batched step 3)
-  unsigned long long cnt[16];
+  unsigned long long cnt[C_NCOUNT];
 };
 
 // A point set with its band/cell structure (sorted order).

@@ -172,6 +172,7 @@ struct MlsArgs {
   double mu[KMAX + 1];
   void* mom;                    // per work-order position: moments (float MIXED, double FP64)
   uint32_t* redo_list;          // MIXED: work-order positions re-solved in FP64
+  uint32_t* reg_list;           // work-order positions with chi > chi_T (solved again with tau)
   int m;                        // dim Pi_K^tan
   int32_t* count;               // M_Q: n(q) = #X(q), written by the gather
   const uint8_t* guarded;       // M_Q: support radius from the guard

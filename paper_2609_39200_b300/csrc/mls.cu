@@ -78,12 +78,14 @@ __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 
 // The local problem from its moments. mw: NM weighted moments, my: NY value
 // moments (unnormalised weights). Returns c1; also chi, tau~, the smallest
-// squared pivot and the number of dropped directions.
+// squared pivot and the number of dropped directions. With defer given, a
+// problem with chi > chi_T stops before the bisection for tau and sets
+// *defer (the caller solves it again, without defer, in a pass of its own).
 // BT: arithmetic of the bisection for tau (FP32 is enough when S = double
 // only serves to make the Cholesky of an ill-conditioned FP32 Gram reliable).
 template <typename S, int K, typename BT = S>
 __device__ __forceinline__ S solve_local(const S* mw, const S* my, const SolveParams& P, S& chi_out, S& tau_out,
-                                         S& minpiv, int& ndrop) {
+                                         S& minpiv, int& ndrop, int* defer = nullptr) {
   constexpr int m = Shape<K>::m, mm = m - 1, D2 = 2 * K, D1 = K;
   const S W = mw[0];
   S is[m];
@@ -165,6 +167,12 @@ __device__ __forceinline__ S solve_local(const S* mw, const S* my, const SolvePa
   const S chi = r0 < S(1) ? S(1) / (S(1) - r0) : inf;
   S tt = S(0);
   const S chiT = S(P.chiT);
+  if (defer && chi > chiT) {
+    *defer = 1;
+    chi_out = chi;
+    tau_out = S(0);
+    return S(0);
+  }
   if (chi > chiT) {
     BT Db[K + 1];
 #pragma unroll
@@ -511,6 +519,9 @@ __global__ void __launch_bounds__(MLS_WARPS * 32, 7) mls_gather_kernel(MlsArgs a
 // Solve: one thread per grid node. MIXED solves in FP32; a node whose FP32
 // Cholesky meets a tiny pivot is appended to a list and re-solved in FP64 by
 // redo_kernel, so the FP64 work runs on full warps instead of diverging here.
+// Likewise a node with chi > chi_T (about one in seven, so nearly every warp
+// holds one) is listed for reg_kernel, which runs the bisection for tau on
+// full warps; the others finish here.
 template <int K, bool MIXED>
 __global__ void __launch_bounds__(128) mls_solve_kernel(MlsArgs a, SolveParams P) {
   using T = typename std::conditional<MIXED, float, double>::type;
@@ -523,10 +534,11 @@ __global__ void __launch_bounds__(128) mls_solve_kernel(MlsArgs a, SolveParams P
 #pragma unroll
   for (int i = 0; i < NV; ++i) mom[i] = act ? src[i] : (i == 0 ? T(1) : T(0));
   T chi, tau, minpiv;
-  int ndrop;
-  const T c1 = solve_local<T, K>(mom, mom + NM, P, chi, tau, minpiv, ndrop);
-  const bool redo = MIXED && act && (ndrop > 0 || !(minpiv >= T(a.fp64_pivot)) || !isfinite(c1));
-  if (act && !redo) {
+  int ndrop, defer = 0;
+  const T c1 = solve_local<T, K>(mom, mom + NM, P, chi, tau, minpiv, ndrop, &defer);
+  const bool redo = MIXED && act && (ndrop > 0 || !(minpiv >= T(a.fp64_pivot)) || (!defer && !isfinite(c1)));
+  const bool reg = act && !redo && defer;
+  if (act && !redo && !reg) {
     const int j = (int)a.order[pos];
     a.fgrid[j] = (double)c1;
     a.chi[j] = (double)chi;
@@ -539,11 +551,59 @@ __global__ void __launch_bounds__(128) mls_solve_kernel(MlsArgs a, SolveParams P
     base = __shfl_sync(FULL, base, 0);
     if (redo) a.redo_list[base + __popc(rb & ((1u << lane) - 1u))] = (uint32_t)pos;
   }
-  const unsigned long long nreg = __popc(__ballot_sync(FULL, act && !redo && tau > T(0)));
-  const unsigned long long nd = warp_sum((unsigned long long)((act && !redo) ? ndrop : 0));
-  if (lane == 0) {
-    if (nreg) atomicAdd(&a.st->cnt[C_REG], nreg);
-    if (nd) atomicAdd(&a.st->cnt[C_DROP], nd);
+  const unsigned gb = __ballot_sync(FULL, reg);
+  if (gb) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&a.st->cnt[C_REG_LIST], (unsigned long long)__popc(gb));
+    base = __shfl_sync(FULL, base, 0);
+    if (reg) a.reg_list[base + __popc(gb & ((1u << lane) - 1u))] = (uint32_t)pos;
+  }
+  const bool done = act && !redo && !reg;
+  const unsigned long long nd = warp_sum((unsigned long long)(done ? ndrop : 0));
+  if (lane == 0 && nd) atomicAdd(&a.st->cnt[C_DROP], nd);
+}
+
+// The listed nodes with chi > chi_T, solved again in full (bisection for
+// tau included; the same arithmetic as a solve that never deferred). MIXED:
+// a value that is not finite sends the node on to the FP64 re-solve.
+template <int K, bool MIXED>
+__global__ void __launch_bounds__(128) reg_kernel(MlsArgs a, SolveParams P) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  constexpr int NV = Shape<K>::NV, NM = Shape<K>::NM, NVP = (NV + 1) & ~1;
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)a.st->cnt[C_REG_LIST];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < total; e0 += stride) {
+    const long long e = e0 + lane;
+    const bool act = e < total;
+    const long long pos = act ? (long long)a.reg_list[e] : 0;
+    const T* src = reinterpret_cast<const T*>(a.mom) + pos * NVP;
+    T mom[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) mom[i] = act ? src[i] : (i == 0 ? T(1) : T(0));
+    T chi, tau, minpiv;
+    int ndrop;
+    const T c1 = solve_local<T, K>(mom, mom + NM, P, chi, tau, minpiv, ndrop);
+    const bool redo = MIXED && act && !isfinite(c1);
+    if (act && !redo) {
+      const int j = (int)a.order[pos];
+      a.fgrid[j] = (double)c1;
+      a.chi[j] = (double)chi;
+      a.tau[j] = (double)tau;
+    }
+    const unsigned rb = __ballot_sync(FULL, redo);
+    if (rb) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(&a.st->cnt[C_REDO_LIST], (unsigned long long)__popc(rb));
+      base = __shfl_sync(FULL, base, 0);
+      if (redo) a.redo_list[base + __popc(rb & ((1u << lane) - 1u))] = (uint32_t)pos;
+    }
+    const unsigned long long nreg = __popc(__ballot_sync(FULL, act && !redo && tau > T(0)));
+    const unsigned long long nd = warp_sum((unsigned long long)((act && !redo) ? ndrop : 0));
+    if (lane == 0) {
+      if (nreg) atomicAdd(&a.st->cnt[C_REG], nreg);
+      if (nd) atomicAdd(&a.st->cnt[C_DROP], nd);
+    }
   }
 }
 
@@ -597,7 +657,8 @@ static void launch_mls(const MlsArgs& a, const SolveParams& P, unsigned long lon
   // the listed positions (usually none) gathered again with their guarded radii
   mls_gather_kernel<K, MIXED, true><<<a.num_sms, MLS_WARPS * 32, 0, s>>>(a, &a.st->cnt[C_LIST_BATCH], 0);
   mls_solve_kernel<K, MIXED><<<(a.MQ + 127) / 128, 128, 0, s>>>(a, P);
-  *launches += 2;
+  reg_kernel<K, MIXED><<<a.num_sms * 8, 128, 0, s>>>(a, P);
+  *launches += 3;
   if (MIXED) {
     redo_kernel<K><<<a.num_sms * 8, 128, 0, s>>>(a, P);
     ++*launches;
