@@ -554,11 +554,21 @@ __global__ void __launch_bounds__(256) shepard_apply_kernel(SupportArgs a) {
   const T* sws = reinterpret_cast<const T*>(a.shep_sw);
   const T* dn = F64 ? reinterpret_cast<const T*>(a.dn_aux_sorted) : reinterpret_cast<const T*>(a.dn_aux_f);
   const float dtyp = 2.f * sqrtf((float)a.n_target / (float)a.nodes.n);
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < MQ; j += gridDim.x * blockDim.x) {
-    const uint32_t e0 = a.shep_start[j], e1 = a.shep_start[j + 1];
+  // four lanes per row (a row holds about a dozen members): interleaved,
+  // coalesced reads of the row, then two shuffles
+  constexpr int G = 4;
+  const int lane = threadIdx.x & 31, g = lane & (G - 1);
+  const int rows_per_pass = gridDim.x * (blockDim.x / G);
+  for (int jw = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / G; jw < MQ; jw += rows_per_pass) {
+    const int j = jw + lane / G;
     T swd = T(0);
-#pragma unroll 4
-    for (uint32_t e = e0; e < e1; ++e) swd += w[e] * dn[a.shep_col[e]];
+    if (j < MQ) {
+      const uint32_t e0 = a.shep_start[j], e1 = a.shep_start[j + 1];
+      for (uint32_t e = e0 + g; e < e1; e += G) swd += w[e] * dn[a.shep_col[e]];
+    }
+    swd += __shfl_xor_sync(FULL, swd, 1);
+    swd += __shfl_xor_sync(FULL, swd, 2);
+    if (j >= MQ || g != 0) continue;
     const T sw = sws[j];
     if (F64) {
       const double PI = 3.14159265358979323846;
@@ -714,7 +724,7 @@ void shepard_rows(const SupportArgs& a, uint32_t* rows, uint32_t* col, void* w, 
 
 void run_shepard(const SupportArgs& a, cudaStream_t s, int64_t* launches) {
   const int MQ = (a.N + 1) * (2 * a.N + 2);
-  const int blocks = (MQ + 255) / 256;
+  const int blocks = (4 * MQ + 255) / 256;   // four lanes per row
   if (a.fp64)
     shepard_apply_kernel<true><<<blocks, 256, 0, s>>>(a);
   else
