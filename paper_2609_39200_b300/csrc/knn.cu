@@ -354,7 +354,7 @@ __device__ int knn_select(const Cells& g, double qx, double qy, double qz, float
 // n-th smallest exact squared chord from q to the points of g (+inf and
 // *failed when there are fewer than n points). r_hint > 0: a radius known to
 // hold at least n points (then one scan suffices); otherwise phase 1 finds one.
-// KL: length of the per-lane lists, 12 for n <= 48, else 16.
+// KL: length of the per-lane lists (8, 12 or 16 for the auxiliary grid by n, 16 elsewhere).
 template <int KL>
 __device__ double knn_nth(const Cells& g, double qx, double qy, double qz, int n, unsigned char* scratch,
                           double r0, bool* failed, KnnTally& tally,
@@ -690,8 +690,15 @@ static void launch_aux_knn(const SupportArgs& a, cudaStream_t s) {
                                                                   &a.st->cnt[C_TILE]);
 }
 
+// Lane lists of 8, 12 or 16 keys: a lane holds about n/32 of the keys up to
+// the n-th, and a list that fills up to the bracket sends the point to the
+// exact search, so the length keeps that rare (n = 40: 1.25 per lane, a
+// lane with 8 of them about 3e-5) while each candidate costs a fixed
+// compare-and-select network of the list's length.
 void run_aux_knn(const SupportArgs& a, cudaStream_t s, int64_t* launches) {
-  if (a.n_target <= 48)
+  if (a.n_target <= 40)
+    launch_aux_knn<8>(a, s);
+  else if (a.n_target <= 48)
     launch_aux_knn<12>(a, s);
   else
     launch_aux_knn<KL_MAX>(a, s);
