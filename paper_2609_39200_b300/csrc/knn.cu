@@ -214,7 +214,7 @@ __device__ __noinline__ float knn_grow_radius(const Cells& g, float qxf, float q
 // smallest FP32 squared chords among the candidates it is dealt (sorted,
 // with indices) - no warp-serialised list. The n-th smallest key T over the
 // warp is bracketed, tl < T <= th, by a search on values that stops once
-// th - tl is within the FP32 error bound m or (tl, th] holds one key. Then
+// th - tl is within the FP32 error bound m or (tl, th] holds at most 8 keys. Then
 // keys < tl - 2m are certainly among the n nearest (A of them), keys above
 // th + 2m certainly not, and the answer is the (n - A)-th smallest exact FP64
 // chord among the keys in [tl - 2m, th + 2m].
@@ -278,7 +278,7 @@ __device__ int knn_select(const Cells& g, double qx, double qy, double qz, float
   // Isolate the n-th smallest key T in a window (tl, th] with cl = count(<= tl)
   // < n <= ch = count(<= th): interpolation on the counts (the keys are
   // roughly uniform in squared chord, i.e. in area), safeguarded to cut at
-  // least an eighth of the window, until the window holds one key or is
+  // least an eighth of the window, until the window holds at most 8 keys or is
   // narrower than the FP32 error bound.
   float th = 0.f;
 #pragma unroll
@@ -286,9 +286,12 @@ __device__ int knn_select(const Cells& g, double qx, double qy, double qz, float
     if (key[s2] < INF_F) th = fmaxf(th, key[s2]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) th = fmaxf(th, __shfl_xor_sync(FULL, th, o));
+  // (at most 8 keys: the exact step below ranks up to 32 in parallel, and
+  // narrowing further costs a count per step, many where the keys of a node
+  // track crowd together)
   float tl = -1e-30f;
   int cl = 0, ch = fin_total;
-  for (int it = 0; it < 48 && ch - cl > 1; ++it) {
+  for (int it = 0; it < 48 && ch - cl > 8; ++it) {
     const float w = th - tl;
     if (w <= c2_margin_f(th)) break;
     float f = __fdividef((float)(n - cl) - 0.5f, (float)(ch - cl));
@@ -335,13 +338,16 @@ __device__ int knn_select(const Cells& g, double qx, double qy, double qz, float
     const uint32_t id = ustage[lane];
     e = chord2_exact(g.px[id], g.py[id], g.pz[id], qx, qy, qz);
   }
+  // ranks on the bit patterns (non-negative doubles and +inf order as
+  // integers), off the FP64 pipe
+  const long long eb = __double_as_longlong(e);
   int rank = 0;
   for (int s2 = 0; s2 < nu; ++s2) {
-    const double o = __shfl_sync(FULL, e, s2);
-    rank += (o < e || (o == e && s2 < lane)) ? 1 : 0;
+    const long long o = __shfl_sync(FULL, eb, s2);
+    rank += (o < eb || (o == eb && s2 < lane)) ? 1 : 0;
   }
   const unsigned hit = __ballot_sync(FULL, lane < nu && rank == n - A - 1);
-  nth = __shfl_sync(FULL, e, __ffs(hit) - 1);
+  nth = __longlong_as_double(__shfl_sync(FULL, eb, __ffs(hit) - 1));
   __syncwarp();
   // every point within geodesic r of q was enumerated; is the n-th inside?
   const float gn = geodesic_f((float)nth);
