@@ -179,7 +179,13 @@ __device__ __noinline__ float knn_initial_radius(const Cells& g, float qxf, floa
   return r;
 }
 
-__device__ __forceinline__ float geodesic_f(float c2) { return 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2))); }
+// FP32 geodesic distance of a squared chord for the search radii and their
+// bounds (each used with a relative margin of 1e-5 or more): the arcsin
+// series below a half-chord of 1/4, asinf (clamped to 1) above
+__device__ __forceinline__ float geodesic_f(float c2) {
+  const float s = 0.5f * sqrtf(c2);
+  return s > 0.25f ? 2.f * asinf(fminf(1.f, s)) : geodesic_series_f(c2);
+}
 
 // A radius beyond r for a cap that held fewer than n points: the enumeration
 // at the new radius (counted from the run table alone) holds about 2 to 8
