@@ -126,7 +126,7 @@ __device__ __forceinline__ S solve_local(const S* mw, const S* my, const SolvePa
     S ljj, inv;
     if (sizeof(S) == 8) {
       inv = drop[j] ? S(0) : rsqrt_t<S>(sjj);
-      ljj = sjj * inv;
+      ljj = drop[j] ? S(0) : sjj * inv;
     } else {
       ljj = drop[j] ? S(0) : sqrt(sjj);
       inv = drop[j] ? S(0) : S(1) / ljj;
@@ -276,7 +276,7 @@ __device__ void solve_gamma(const double* mw, const SolveParams& P, double* gamm
     drop[j] = !(sjj > S(P.floor_));
     // as solve_local's FP64 form: 1/l_jj by one reciprocal square root
     inv[j] = drop[j] ? S(0) : rsqrt_t<S>(sjj);
-    L[tri(j, j)] = sjj * inv[j];
+    L[tri(j, j)] = drop[j] ? S(0) : sjj * inv[j];
 #pragma unroll
     for (int i = j + 1; i < mm; ++i) {
       S v = L[tri(i, j)];
