@@ -35,10 +35,10 @@ WORKLOAD = "s2_n512_k3_m4m"
 # stage's dominant kernel from an ncu capture (see profiles/); a stage whose
 # kernel changed after that capture has no entry and reports null.
 TRAFFIC = {
-    # profiles/aux_knn_kernel_s2_n512_k3_m4m.md: 194.0 MB read + 21.3 MB written
-    "aux_knn": 215_310_080,
-    # profiles/mls_gather_kernel_s2_n512_k3_m4m.md (the MLS stage's main kernel): 80.6 + 50.4 MB
-    "mls": 131_017_472,
+    # profiles/aux_knn_kernel_s2_n512_k3_m4m.md: 199.7 MB read + 21.7 MB written
+    "aux_knn": 221_427_200,
+    # profiles/mls_gather_kernel_s2_n512_k3_m4m.md (the MLS stage's main kernel): 80.7 + 49.5 MB
+    "mls": 130_120_192,
 }
 
 
