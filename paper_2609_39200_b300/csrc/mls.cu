@@ -402,7 +402,9 @@ __device__ __forceinline__ void reduce_scatter(const T (&acc)[NV], T (&out)[2], 
 // The gather also counts n(q) = #X(q) (eq. number_of_local_nodes) and lists
 // the positions with n(q) < m for the guard. LIST = true gathers only the
 // listed positions again, after the guard has widened their supports.
-template <int K, bool MIXED, bool LIST>
+// WF: the weight function (0 phi_{3,2}, 1 phi_{3,1}) as a constant of the
+// instance, so a member's weight is one polynomial with no selection.
+template <int K, bool MIXED, bool LIST, int WF>
 // 7 blocks of 4 warps per SM (at most 72 registers): more warps hide the
 // gather's L2 latency better than the registers they cost
 __global__ void __launch_bounds__(MLS_WARPS * 32, 7) mls_gather_kernel(MlsArgs a, unsigned long long* ctr,
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(MLS_WARPS * 32, 7) mls_gather_kernel(MlsArgs a
           const float c2 = dx * dx + dy * dy + dz * dz;
           if (!(c2 < r2f)) return;
           ++nin;
-          float w = weight_phi(a.weight_fn, geodesic_series_f(c2) * idf);
+          float w = weight_phi(WF, geodesic_series_f(c2) * idf);
           if (a.swf) w *= a.swf[idx];
           const float u = e1x * dx + e1y * dy + e1z * dz;
           const float v = e2x * dx + e2y * dy;
@@ -478,7 +480,7 @@ __global__ void __launch_bounds__(MLS_WARPS * 32, 7) mls_gather_kernel(MlsArgs a
           if (!(c2 < rho2)) return;
           ++nin;
           const double dx = X - qx, dy = Y - qy, dz = Z - qz;
-          double w = weight_phi(a.weight_fn, geodesic_from_chord2(c2) * id);
+          double w = weight_phi(WF, geodesic_from_chord2(c2) * id);
           if (a.sw) w *= a.sw[idx];
           const double u = e1x * dx + e1y * dy + e1z * dz;
           const double v = e2x * dx + e2y * dy;
@@ -642,20 +644,32 @@ __global__ void __launch_bounds__(128) redo_kernel(MlsArgs a, SolveParams P) {
   }
 }
 
+template <int K, bool MIXED, int WF>
+static void launch_gather(const MlsArgs& a, unsigned long long* ctr, cudaStream_t s, int part) {
+  if (part == 1) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mls_gather_kernel<K, MIXED, false, WF>, MLS_WARPS * 32,
+                                                  0);
+    if (per_sm < 1) per_sm = 1;
+    const long long heavy = a.MQ < 4096 ? a.MQ : (a.MQ / 8 > 4096 ? a.MQ / 8 : 4096);
+    mls_gather_kernel<K, MIXED, false, WF><<<per_sm * a.num_sms, MLS_WARPS * 32, 0, s>>>(a, ctr, heavy);
+  } else {
+    // the listed positions (usually none) gathered again with their guarded radii
+    mls_gather_kernel<K, MIXED, true, WF><<<a.num_sms, MLS_WARPS * 32, 0, s>>>(a, &a.st->cnt[C_LIST_BATCH], 0);
+  }
+}
+
 template <int K, bool MIXED>
 static void launch_mls(const MlsArgs& a, const SolveParams& P, unsigned long long* ctr, cudaStream_t s,
                        int64_t* launches, int part) {
+  if (a.weight_fn == 1)
+    launch_gather<K, MIXED, 1>(a, ctr, s, part);
+  else
+    launch_gather<K, MIXED, 0>(a, ctr, s, part);
   if (part == 1) {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mls_gather_kernel<K, MIXED, false>, MLS_WARPS * 32, 0);
-    if (per_sm < 1) per_sm = 1;
-    const long long heavy = a.MQ < 4096 ? a.MQ : (a.MQ / 8 > 4096 ? a.MQ / 8 : 4096);
-    mls_gather_kernel<K, MIXED, false><<<per_sm * a.num_sms, MLS_WARPS * 32, 0, s>>>(a, ctr, heavy);
     ++*launches;
     return;
   }
-  // the listed positions (usually none) gathered again with their guarded radii
-  mls_gather_kernel<K, MIXED, true><<<a.num_sms, MLS_WARPS * 32, 0, s>>>(a, &a.st->cnt[C_LIST_BATCH], 0);
   mls_solve_kernel<K, MIXED><<<(a.MQ + 127) / 128, 128, 0, s>>>(a, P);
   reg_kernel<K, MIXED><<<a.num_sms * 8, 128, 0, s>>>(a, P);
   *launches += 3;
