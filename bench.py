@@ -37,8 +37,8 @@ WORKLOAD = "s2_n512_k3_m4m"
 TRAFFIC = {
     # profiles/aux_knn_kernel_s2_n512_k3_m4m.md: 199.7 MB read + 21.7 MB written
     "aux_knn": 221_427_200,
-    # profiles/mls_gather_kernel_s2_n512_k3_m4m.md (the MLS stage's main kernel): 80.7 + 49.5 MB
-    "mls": 130_120_192,
+    # profiles/mls_gather_kernel_s2_n512_k3_m4m.md (the MLS stage's main kernel): 80.6 + 49.2 MB
+    "mls": 129_811_200,
 }
 
 
